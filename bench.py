@@ -1,0 +1,446 @@
+#!/usr/bin/env python
+"""Tracked + fused frames/s of the pose search and fusion hot path.
+
+Workload: a 30 Hz synthetic trajectory of 640x480 depth frames (f = 525,
+c = (319.5, 239.5), noise sigma = 0.0012 z^2) through an analytic two-room
+scene held in a 512^3 TSDF at 1 cm (truncation 3 cm, f32 tsdf + f32 weight);
+every frame runs the randomized pose search (3072 particles x 20 iterations
+over all valid points, advantage-set update) from a ground-truth relative
+pose perturbed by 3 deg / 3 cm, then fuses the frame.  One step = one frame.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+value      frames/s with every depth frame resident in HBM (CUDA events around
+           K back-to-back device-resident frames; no host round trip).
+e2e        the same frames through the host API (pinned depth H2D, pose and
+           stats D2H per frame), wall clock.
+roofline   of the dominant kernel (the fitness gather-reduce), from CUDA
+           events around each of its launches during the timed region.
+Multi-GPU: the path does not shard within a frame; N ranks run N independent
+sequences (replicas) and value = all frames / max time over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "tracked+fused frames/s (640x480, 512^3 TSDF); point-particle samples/s vs plain FP32"
+K_PARTICLES = 3072
+N_ITERS = 20
+# FP32 work of one sample (one point under one particle): transform 9 FMA,
+# fractional cell coordinates 3 subtractions, 7 linear interpolations
+# (1 subtraction + 1 FMA each), |.| accumulation 1 add; FMA counted as 2.
+FLOP_PER_SAMPLE = 9 * 2 + 3 + 7 * 3 + 1
+GATHER_BYTES_PER_SAMPLE = 8 * 4  # eight f32 nodes
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--variant", type=int, default=0, help="fitness kernel: 0 encoded (default), 1 plain")
+    ap.add_argument("--update-mode", type=int, default=0)
+    ap.add_argument("--compose-mode", type=int, default=1)
+    ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--ref-particles", type=int, default=192,
+                    help="particles per reference-arm step (a bounded slice of one iteration)")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------------------
+# inputs
+# ---------------------------------------------------------------------------
+
+def _render(args):
+    import synth
+    n_frames, seed, f = args
+    seq = synth.multiroom_sequence(n_frames, seed)
+    return seq.depth(f), seq.relative_init(f) if f > 0 else np.eye(4)
+
+
+def render_frames(n_needed: int, seed: int):
+    """Depth frames 0..n_needed-1 and perturbed relative poses, rendered in a
+    spawn pool (started before any CUDA call)."""
+    import multiprocessing as mp
+
+    import synth
+    seq = synth.multiroom_sequence(300, seed)
+    jobs = [(300, seed, f) for f in range(n_needed)]
+    workers = max(1, min(len(jobs), (os.cpu_count() or 2) - 1, 16))
+    if workers > 1:
+        with mp.get_context("spawn").Pool(workers) as pool:
+            out = pool.map(_render, jobs)
+    else:
+        out = [_render(j) for j in jobs]
+    depths = [o[0] for o in out]
+    rels = [o[1] for o in out]
+    return seq, depths, rels
+
+
+# ---------------------------------------------------------------------------
+# clocks
+# ---------------------------------------------------------------------------
+
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        import tempfile
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.QUERY}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+        sm = [num(r[1]) for r in rows if num(r[1]) is not None]
+        mx = [num(r[2]) for r in rows if num(r[2]) is not None]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            for name, val in zip(names, r[5:9]):
+                if val.strip().lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(rows),
+                "power_w_max": max([num(r[3]) for r in rows if num(r[3]) is not None], default=None)}
+
+
+# ---------------------------------------------------------------------------
+# the oracle on the host cores
+# ---------------------------------------------------------------------------
+
+def oracle_sample(seq, depths, rels, compose_mode: int, n_particles: int, repeats: int = 1):
+    """Oracle timing on a bounded sample of the workload: fuse frame 0 (not
+    timed), then time `repeats` evaluations of `n_particles` particles of one
+    search iteration of frame 1 over all its points, and the fusion of frame 1.
+    Returns (frames/s extrapolated to 3072 particles x 20 iterations + fusion,
+    description, cores, per-repeat timings)."""
+    import oracle
+    import synth
+    oracle.build()
+    grid, intr = seq.grid, seq.intr
+    vol = oracle.Volume(grid)
+    oracle.integrate(vol, depths[0], intr, seq.gt[0])
+    P0 = seq.gt[0] @ rels[1]
+    pts = oracle.backproject(depths[1], intr)
+    templ = synth.templates(K_PARTICLES, 0)
+    T = oracle.particles(templ, K_PARTICLES, P0, 10.0, 10.0, compose_mode)
+    times = []
+    for r in range(repeats):
+        lo = (r * n_particles) % K_PARTICLES
+        sel = T[lo:lo + n_particles]
+        t0 = time.perf_counter()
+        oracle.fitness(vol, pts, sel)
+        times.append(time.perf_counter() - t0)
+    vol2 = oracle.Volume(grid, vol.tsdf.copy(), vol.weight.copy())
+    t0 = time.perf_counter()
+    oracle.integrate(vol2, depths[1], intr, P0)
+    t_int = time.perf_counter() - t0
+    t_particle = float(np.median(times)) / n_particles
+    t_frame = N_ITERS * (K_PARTICLES + 1) * t_particle + t_int
+    desc = (f"oracle (C, FP64, OpenMP): fusion of frame 0 untimed; timed {repeats}x fitness of {n_particles} "
+            f"particles over all {pts.shape[0]} points of frame 1 and one 512^3 fusion; per-frame time "
+            f"extrapolated to {N_ITERS} x ({K_PARTICLES}+1) particle evaluations + 1 fusion")
+    return 1.0 / t_frame, desc, oracle.num_threads(), times, t_int, pts.shape[0]
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    steps, warm = max(1, args.steps), max(0, args.warmup)
+    seq, depths, rels = render_frames(2, args.seed)
+    fps, desc, cores, times, t_int, npts = oracle_sample(seq, depths, rels, args.compose_mode, args.ref_particles,
+                                                         repeats=steps + warm)
+    times = times[warm:]
+    t_particle = float(np.mean(times)) / args.ref_particles
+    t_frame = N_ITERS * (K_PARTICLES + 1) * t_particle + t_int
+    value = 1.0 / t_frame
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "frames/s", "n_gpus": args.gpus,
+        "steps": steps, "warmup": warm, "ms_per_step": 1e3 * t_frame, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": workload_config(args),
+        "cpu_baseline": {"value": value, "unit": "frames/s", "cores": cores, "kind": "oracle",
+                         "sample": desc.replace(f"timed {steps + warm}x", f"timed {steps}x (after {warm} warm-up)")},
+        "e2e": {"value": value, "unit": "frames/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "samples_per_s": npts / t_particle,
+    }
+    print(json.dumps(line))
+    return 0
+
+
+def workload_config(args) -> dict:
+    return {
+        "workload": "multiroom: 640x480 depth, 512^3 TSDF @ 1 cm (tau 3 cm, f32 tsdf + f32 weight), "
+                    "3072 particles x 20 iterations over all points, then fusion",
+        "resolution": "640x480", "volume": "512^3", "voxel_m": 0.01, "trunc_m": 0.03,
+        "particles": K_PARTICLES, "iterations": N_ITERS, "decimation": 1,
+        "update": "advantage-set mean" if args.update_mode == 0 else "best particle",
+        "compose": "about the world origin" if args.compose_mode == 0 else "about the camera centre",
+        "init_perturbation": "3 deg / 3 cm", "seed": args.seed,
+        "l2": "inputs larger than L2: fusion reads and writes the 1.07 GB volume frustum every step",
+        "parallelism": f"replicas x{args.gpus}",
+    }
+
+
+# ---------------------------------------------------------------------------
+# our path
+# ---------------------------------------------------------------------------
+
+def run_ours(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    W, K = max(3, args.warmup), max(1, args.steps)
+    n_frames = 1 + W + K
+    if n_frames > 300:
+        raise SystemExit("--warmup + --steps must be <= 299 (300-frame trajectory)")
+    seq, depths, rels = render_frames(n_frames, args.seed + rank)
+
+    import torch
+    import paper_2509_24236_gb300 as pf
+    from paper_2509_24236_gb300 import build as pfbuild
+    pfbuild.build()
+    pf.load()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    intr, grid = seq.intr, seq.grid
+    stream = torch.cuda.current_stream()
+    vol = pf.Volume.from_grid(grid)
+    vol.set_fitness_variant(args.variant)
+    vol.reserve(intr.width * intr.height, K_PARTICLES)
+    import synth
+    templ = torch.from_numpy(synth.templates(K_PARTICLES, args.seed)).to(dev)
+    params = pf.track_params(templ, n_iters=N_ITERS, k_sched=(K_PARTICLES,) * 3, decim_sched=(1, 1, 1),
+                             update_mode=args.update_mode, compose_mode=args.compose_mode, min_valid_frac=0.05)
+    depth_dev = [torch.from_numpy(d).to(dev) for d in depths]
+    rel_dev = torch.from_numpy(np.stack([r.reshape(16) for r in rels])).to(dev)
+    init_dev = torch.zeros((n_frames, 16), dtype=torch.float64, device=dev)
+    pose_dev = torch.zeros((n_frames, 16), dtype=torch.float64, device=dev)
+    stats_sz = __import__("ctypes").sizeof(pf.pf_track_stats)
+    stats_dev = torch.zeros((n_frames, stats_sz), dtype=torch.uint8, device=dev)
+    pose_dev[0] = torch.from_numpy(seq.gt[0].reshape(16)).to(dev)
+
+    def device_frame(f):
+        pf.pf_pose_compose(pose_dev[f - 1], rel_dev[f], init_dev[f])
+        vol.track_frame_async(depth_dev[f], intr, params, init_dev[f], pose_dev[f], stats_dev[f])
+        vol.integrate_async(depth_dev[f], intr, pose_dev[f])
+
+    # ---- device-resident pass -------------------------------------------
+    vol.integrate_async(depth_dev[0], intr, pose_dev[0])
+    for f in range(1, W + 1):
+        device_frame(f)
+    torch.cuda.synchronize()
+    barrier()
+    pf.pf_set_kernel_timing(True)
+    for cls in ("fitness", "fitness1", "integrate", "backproject"):
+        pf.pf_kernel_timing(cls)
+    clocks = ClockSampler(local)
+    clocks.start()
+    launches0 = pf.pf_launch_count()
+    torch.cuda.synchronize()
+    barrier()
+    t_begin = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    t_begin.record(stream)
+    for f in range(W + 1, W + K + 1):
+        device_frame(f)
+    t_end.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    launches = pf.pf_launch_count() - launches0
+    clock_info = clocks.stop()
+    ms = t_begin.elapsed_time(t_end)
+    kt = {cls: pf.pf_kernel_timing(cls) for cls in ("fitness", "fitness1", "integrate", "backproject")}
+    pf.pf_set_kernel_timing(False)
+    ms_max = ms
+    if dist is not None:
+        t = torch.tensor([ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_max = float(t.item())
+
+    # per-frame statistics of the timed frames
+    stats_host = stats_dev.cpu().numpy()
+    samples = 0
+    n_lost = 0
+    for f in range(W + 1, W + K + 1):
+        st = pf.pf_track_stats.from_buffer_copy(stats_host[f].tobytes()).to_dict()
+        samples += int(np.sum(st["k_used"].astype(np.int64) * st["n_eval"]))
+        n_lost += int(st["status"] == pf.PF_ERR_TRACK_LOST)
+    poses = pose_dev.cpu().numpy().reshape(-1, 4, 4)
+    err = [np.linalg.norm(poses[f][:3, 3] - seq.gt[f][:3, 3]) for f in range(1, W + K + 1)]
+    ate_cm = 100.0 * float(np.sqrt(np.mean(np.square(err))))
+
+    # ---- fitness kernel throughput, encoded vs plain layout --------------
+    vs_plain = fitness_vs_plain(pf, vol, depth_dev[W + 1], intr, poses[W], dev)
+
+    # ---- end-to-end pass through the host API ----------------------------
+    e2e = None
+    if not args.no_e2e:
+        e2e = run_e2e(pf, vol, seq, depths, rels, intr, params, W, K, dev)
+
+    total_frames = K * world
+    value = total_frames / (ms_max / 1e3)
+    fit_ms, fit_n = kt["fitness"]
+    fit_avg_ms = fit_ms / max(1, fit_n)
+    samples_per_launch = samples / max(1, fit_n)
+    achieved_tflops = samples_per_launch * FLOP_PER_SAMPLE / (fit_avg_ms / 1e3) / 1e12
+    peak_tflops = fp32_peak_tflops()
+    line = {
+        "metric": METRIC, "value": value, "unit": "frames/s", "n_gpus": world, "steps": K, "warmup": W,
+        "ms_per_step": ms_max / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic", "config": workload_config(args),
+        "samples_per_s": samples / (ms / 1e3),
+        "fitness_samples_per_s": samples / (fit_ms / 1e3) if fit_ms > 0 else None,
+        "fitness_vs_plain": vs_plain,
+        "roofline": {"bound": "alu", "kernel": "fitness_kernel<search>", "achieved": achieved_tflops,
+                     "peak": peak_tflops, "unit": "TFLOP/s", "frac": achieved_tflops / peak_tflops,
+                     "traffic": None, "avg_launch_ms": fit_avg_ms, "launches": fit_n,
+                     "flop_per_sample": FLOP_PER_SAMPLE, "samples_per_launch": samples_per_launch,
+                     "peak_source": "FP32 lanes x clock: 152 SMs x 128 x 2 flop x 2070 MHz (derived)"},
+        "kernel_ms": {cls: {"total_ms": v[0], "launches": v[1]} for cls, v in kt.items()},
+        "gpu_launches": launches,
+        "clocks": clock_info,
+        "ate_cm": ate_cm, "frames_lost": n_lost,
+        "e2e": e2e,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        fps, desc, cores, times, t_int, npts = oracle_sample(seq, depths, rels, args.compose_mode, 48, repeats=1)
+        line["cpu_baseline"] = {"value": fps, "unit": "frames/s", "cores": cores, "kind": "oracle", "sample": desc}
+    if rank == 0:
+        print(json.dumps(line))
+    vol.close()
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def fp32_peak_tflops() -> float:
+    return 152 * 128 * 2 * 2.070e9 / 1e12
+
+
+def fitness_vs_plain(pf, vol, depth, intr, pose, dev, reps=5):
+    """Samples/s of pf_fitness with 3072 poses around `pose` over one frame's
+    points: the encoded (default) kernel against the plain f32 one."""
+    import torch
+
+    import synth
+    pts, n = pf.backproject(depth, intr)
+    n = int(n.item())
+    pts = pts[:n].contiguous()
+    u = synth.uniform01(77, 2 * K_PARTICLES)
+    P = np.stack([(pose @ synth.perturbation(78, k, 10.0 * u[2 * k], 10.0 * u[2 * k + 1]))[:3, :4].reshape(12)
+                  for k in range(K_PARTICLES)]).astype(np.float32)
+    poses = torch.from_numpy(P).to(dev)
+    out = {}
+    for variant, name in ((0, "encoded"), (1, "plain")):
+        vol.set_fitness_variant(variant)
+        vol.fitness(pts, poses)
+        torch.cuda.synchronize()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(reps):
+            vol.fitness(pts, poses)
+        b.record()
+        torch.cuda.synchronize()
+        out[name] = reps * n * K_PARTICLES / (a.elapsed_time(b) / 1e3)
+    vol.set_fitness_variant(0)
+    out["ratio"] = out["encoded"] / out["plain"]
+    out["points"] = n
+    return out
+
+
+def run_e2e(pf, vol, seq, depths, rels, intr, params, W, K, dev):
+    import torch
+    vol.reset()
+    pinned = [torch.from_numpy(d).pin_memory() for d in depths]
+    buf = torch.empty_like(pinned[0], device=dev)
+    P = seq.gt[0].copy()
+    buf.copy_(pinned[0], non_blocking=True)
+    vol.integrate(buf, intr, P)
+
+    def frame(f, P):
+        buf.copy_(pinned[f], non_blocking=True)
+        P0 = P @ rels[f]
+        status, P, _ = vol.track_frame(buf, intr, params, P0)
+        vol.integrate(buf, intr, P)
+        return P
+
+    for f in range(1, W + 1):
+        P = frame(f, P)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for f in range(W + 1, W + K + 1):
+        P = frame(f, P)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    h2d = depths[0].nbytes + 16 * 8
+    d2h = 16 * 8 + __import__("ctypes").sizeof(pf.pf_track_stats)
+    return {"value": K / dt, "unit": "frames/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,256 @@
+/*
+ * profusion.h -- C ABI of the GB300 (sm_103a) library for the dense
+ * reconstruction back end of PROFusion (arXiv 2509.24236): randomized SE(3)
+ * pose search against a TSDF (Sec. III-B) and KinectFusion-style projective
+ * TSDF fusion (Sec. III, "Method overview").
+ *
+ * Conventions used by every call
+ *   - Camera frame: x right, y down, z forward.  Pixel (u, v) are integer
+ *     indices at pixel centres; depth is the camera z coordinate in metres.
+ *     A depth value is usable when finite and in [depth_min, depth_max].
+ *   - Poses are camera-to-world, X_w = R X_c + t (Sec. III: P_t = [R_t | t_t]
+ *     in the world coordinate system).  4x4 poses are row-major double[16]
+ *     (last row 0 0 0 1, not read); fitness poses are row-major float[12]
+ *     (the 3x4 block).  Units: metres, radians (search sizes: degrees, cm).
+ *   - Volume: nx*ny*nz nodes at origin + voxel_size*(i, j, k), flattened
+ *     x-fastest (i + nx*(j + ny*k)).  The TSDF is stored divided by the
+ *     truncation tau, so values lie in [-1, 1]; a node with weight 0 is
+ *     unobserved.
+ *   - Pointers named *_dev are device pointers owned by the caller; *_host
+ *     are host pointers owned by the caller.  The library never frees caller
+ *     memory.  The library owns the volume's device memory and its workspace
+ *     from pf_create_volume until pf_destroy_volume.
+ *   - cuda_stream is a cudaStream_t passed as void*; NULL is the legacy
+ *     default stream.  All kernels of a call are enqueued on that stream.
+ *   - Errors: every call returns pf_status and never aborts.  Arguments are
+ *     validated on the host before anything is enqueued (PF_ERR_INVALID_ARG,
+ *     nothing enqueued).  A CUDA API failure returns PF_ERR_CUDA; faults of
+ *     already-enqueued kernels surface at the next call that synchronises.
+ *   - Determinism: identical inputs on the same stream give bit-identical
+ *     outputs (fixed reduction orders, no floating-point atomics).
+ *   - Concurrency: calls that use the same volume must not overlap on
+ *     different streams (they share its workspace).
+ */
+#ifndef PROFUSION_H
+#define PROFUSION_H
+
+#if defined(__GNUC__)
+#define PF_API __attribute__((visibility("default")))
+#else
+#define PF_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    PF_OK = 0,
+    PF_ERR_INVALID_ARG = 1,
+    PF_ERR_OOM = 2,
+    PF_ERR_CUDA = 3,
+    PF_ERR_TIMEOUT = 4,
+    PF_ERR_TRACK_LOST = 5,
+    PF_ERR_UNSUPPORTED = 6
+} pf_status;
+
+/* Pinhole intrinsics of a depth image (Sec. III, "known camera intrinsic
+ * parameters").  width, height >= 1; fx, fy > 0; 0 < depth_min <= depth_max. */
+typedef struct {
+    int width, height;
+    float fx, fy, cx, cy;
+    float depth_min, depth_max;
+} pf_intrinsics;
+
+/* Storage type of the TSDF values.  This version stores PF_F32 only; other
+ * values are rejected with PF_ERR_UNSUPPORTED. */
+typedef enum { PF_F32 = 0, PF_F16 = 1, PF_BF16 = 2, PF_FP8E4M3 = 3 } pf_dtype;
+
+/* Dense TSDF grid (Sec. III: "a tensor that records the distance value in
+ * each 3D grid").  nx, ny, nz in [2, 4096] with nx*ny*nz < 2^31;
+ * voxel_size > 0; trunc (tau, metres) > 0; max_weight in [1, 65535] caps the
+ * running-average weight; weight_u8 must be 0 in this version. */
+typedef struct {
+    int nx, ny, nz;
+    float voxel_size;
+    float trunc;
+    float origin[3];
+    pf_dtype tsdf_dtype;
+    int weight_u8;
+    int max_weight;
+} pf_volume_desc;
+
+/* Parameters of the randomized optimization (Sec. III-B, defaults Sec. IV-A:
+ * n_iters 20, k_sched {1024, 3072, 10240}, decim_sched {8, 16, 32},
+ * init 10 deg / 10 cm, beta 0.1).
+ *   n_iters        1..PF_MAX_ITERS iterations, no early exit.
+ *   k_sched[i%3]   particles of iteration i (1..k_max; particle 0 = current
+ *                  pose), decim_sched[i%3] keeps every n-th valid point (>= 1).
+ *   templates_dev  k_max x 6 floats (device): row k = (rx, ry, rz, tx, ty, tz),
+ *                  the delta pose of particle k in units of the search size;
+ *                  row 0 must be zero.  Delta pose = [Exp(omega*pi/180*r) |
+ *                  v/100*t].
+ *   update_mode    0: pose <- mean of the advantage set {k : E_k < E_0}
+ *                  composed onto the pose (the paper's update);
+ *                  1: pose <- best particle.
+ *   compose_mode   0: dP * P as written (rotation about the world origin);
+ *                  1: rotation about the camera centre (R' = dR R, t' = t + dt).
+ *   min_valid_frac the frame is lost when particle 0 of the first iteration
+ *                  has fewer than this fraction of the evaluated points valid
+ *                  (or none). */
+typedef struct {
+    int n_iters;
+    int k_sched[3];
+    int decim_sched[3];
+    double init_rot_deg, init_trans_cm, beta;
+    const float* templates_dev;
+    int k_max;
+    int update_mode;
+    int compose_mode;
+    float min_valid_frac;
+} pf_track_params;
+
+#define PF_MAX_ITERS 32
+
+/* Per-frame record of the search; entries [0, n_iters) are filled.
+ * E values are fitness (mean |tsdf| over valid points, +inf if none). */
+typedef struct {
+    int n_points;                   /* valid back-projected points (all, before decimation) */
+    int n_iters;                    /* iterations run */
+    int status;                     /* PF_OK or PF_ERR_TRACK_LOST */
+    int reserved;
+    float E0[PF_MAX_ITERS];         /* fitness of the pose entering iteration i (particle 0) */
+    float E_best[PF_MAX_ITERS];     /* smallest particle fitness */
+    float E_new[PF_MAX_ITERS];      /* fitness of the updated pose (search-size update) */
+    int best[PF_MAX_ITERS];         /* index of the best particle (lowest among ties) */
+    int n_adv[PF_MAX_ITERS];        /* size of the advantage set */
+    int n_valid0[PF_MAX_ITERS];     /* valid points of particle 0 */
+    int n_eval[PF_MAX_ITERS];       /* points evaluated (after decimation) */
+    int k_used[PF_MAX_ITERS];       /* particles evaluated */
+    double s[PF_MAX_ITERS][2];      /* search size (deg, cm) used in iteration i */
+    double pose[PF_MAX_ITERS][12];  /* pose after iteration i, row-major 3x4 */
+} pf_track_stats;
+
+typedef struct pf_volume pf_volume;
+
+/* Allocate a volume on the current device, all nodes unobserved.
+ * Errors: INVALID_ARG (bad desc or out == NULL), UNSUPPORTED (dtype/weight
+ * storage not provided), OOM, CUDA. */
+PF_API pf_status pf_create_volume(const pf_volume_desc* desc, void* cuda_stream, pf_volume** out);
+
+/* Free the volume and its workspace (synchronises the device). NULL is OK. */
+PF_API pf_status pf_destroy_volume(pf_volume* vol);
+
+/* Mark every node unobserved (asynchronous on cuda_stream). */
+PF_API pf_status pf_reset_volume(pf_volume* vol, void* cuda_stream);
+
+/* Copy a whole grid in from / out to host float arrays of nx*ny*nz values:
+ * normalised tsdf and weight (weight 0 = unobserved; download reports tsdf 1
+ * there).  Synchronous; intended for tests and checkpoints. */
+PF_API pf_status pf_volume_upload(pf_volume* vol, const float* tsdf_host, const float* weight_host);
+PF_API pf_status pf_volume_download(const pf_volume* vol, float* tsdf_host, float* weight_host);
+
+/* Fuse one depth image (height x width floats, row-major, device) taken at
+ * cam_to_world into the volume (Sec. III fusion, KinectFusion rule): every
+ * node with camera depth z_c > 0 projecting to pixel (floor(u+1/2),
+ * floor(v+1/2)) inside the image with a usable depth d gets sdf = d - z_c; if
+ * sdf >= -tau it is averaged in as t = min(1, sdf/tau) with weight 1:
+ * tsdf <- (w tsdf + t)/(w + 1), w <- min(w + 1, max_weight). */
+PF_API pf_status pf_integrate(pf_volume* vol, const float* depth_dev, const pf_intrinsics* intr,
+                       const double cam_to_world[16], void* cuda_stream);
+
+/* As pf_integrate, with the pose in device memory (double[16]); nothing
+ * synchronises, so a frame's search and fusion can run back to back on the
+ * device (and be captured in a CUDA graph). */
+PF_API pf_status pf_integrate_async(pf_volume* vol, const float* depth_dev, const pf_intrinsics* intr,
+                                    const double* cam_to_world_dev, void* cuda_stream);
+
+/* out_dev = a_dev * b_dev for row-major 4x4 double poses in device memory,
+ * in FP64: the initial pose of a frame, P_t^(0) = P_{t-1} P_(t,t-1)
+ * (Sec. III-A).  out_dev may alias neither input. */
+PF_API pf_status pf_pose_compose(const double* a_dev, const double* b_dev, double* out_dev, void* cuda_stream);
+
+/* Back-project a depth image into metric camera-frame points (Sec. III,
+ * problem setting): pixel (u, v) with usable depth z gives
+ * ((u - cx) z / fx, (v - cy) z / fy, z).  Points of usable pixels are
+ * written in row-major pixel order as float4 (x, y, z, 0) to points_dev
+ * (capacity entries, >= width*height); the count is written to *n_dev
+ * (device int).  No decimation (the search applies its stride itself). */
+PF_API pf_status pf_backproject(const float* depth_dev, const pf_intrinsics* intr, float* points_dev,
+                         int capacity, int* n_dev, void* cuda_stream);
+
+/* Fitness of k poses against n points (Sec. III-B):
+ * E_k = (1/|X_k|) sum_{x in X_k} |tsdf(T_k x)| with trilinear lookup, where
+ * X_k holds the points whose containing cell lies inside the grid with all
+ * eight nodes observed and within the truncation (|tsdf| < 1).
+ *   points_dev  n x 4 floats (x, y, z, ignored), camera frame.
+ *   poses_dev   k x 12 floats, row-major 3x4 camera-to-world.
+ *   fitness_dev k floats: E_k (+inf when X_k is empty); count_dev k ints: |X_k|.
+ * n >= 0 (n = 0 gives +inf / 0), 1 <= k <= 65536. */
+PF_API pf_status pf_fitness(const pf_volume* vol, const float* points_dev, int n, const float* poses_dev,
+                     int k, float* fitness_dev, int* count_dev, void* cuda_stream);
+
+/* Randomized pose optimization of one frame (Sec. III-B): back-projects the
+ * depth, then runs params->n_iters iterations of sample / evaluate / select /
+ * update, starting from init_pose with search size (init_rot_deg,
+ * init_trans_cm).  Pose composition and re-orthonormalisation run in FP64 on
+ * the device.  out_pose receives the refined pose, or init_pose when the
+ * frame is lost (then PF_ERR_TRACK_LOST is returned).  stats_or_null
+ * receives the per-iteration record.  Synchronises cuda_stream.
+ * The first call on a volume (or one with a larger frame or k_max) allocates
+ * workspace. */
+PF_API pf_status pf_track_frame(pf_volume* vol, const float* depth_dev, const pf_intrinsics* intr,
+                         const pf_track_params* params, const double init_pose[16], double out_pose[16],
+                         pf_track_stats* stats_or_null, void* cuda_stream);
+
+/* As pf_track_frame, but init_pose_dev / out_pose_dev (double[16]) and the
+ * optional stats live in device memory and nothing synchronises, so the call
+ * can be captured in a CUDA graph once the workspace exists (call
+ * pf_track_reserve or one pf_track_frame first).  The lost status is
+ * stats->status; out_pose_dev then holds init_pose_dev. */
+PF_API pf_status pf_track_frame_async(pf_volume* vol, const float* depth_dev, const pf_intrinsics* intr,
+                               const pf_track_params* params, const double* init_pose_dev,
+                               double* out_pose_dev, pf_track_stats* stats_dev_or_null,
+                               void* cuda_stream);
+
+/* Allocate the tracking workspace for frames up to max_pixels pixels and up
+ * to k_max particles (synchronous). */
+PF_API pf_status pf_track_reserve(pf_volume* vol, int max_pixels, int k_max);
+
+/* Ray-cast the fused surface seen from cam_to_world: for each pixel, march
+ * camera depths z_i = depth_min + i * (trunc/2) up to depth_max through the
+ * trilinear field of observed cells; the first step from a positive to a
+ * non-positive value is refined by linear interpolation.  depth_out_dev
+ * (height x width floats) gets that depth or 0; normal_out_dev_or_null
+ * (height x width x 3 floats) gets the unit world-frame gradient there
+ * (central differences at +-voxel/2) or NaN. */
+PF_API pf_status pf_raycast(const pf_volume* vol, const pf_intrinsics* intr, const double cam_to_world[16],
+                     float* depth_out_dev, float* normal_out_dev_or_null, void* cuda_stream);
+
+/* Fitness kernel variant used by pf_fitness and the search of this volume:
+ * 0 (default) reads only the tsdf array, whose encoding makes a cell's
+ * validity a property of its interpolated value; 1 is the plain form that
+ * also reads the weights and tests all eight nodes explicitly.  Results are
+ * identical; the plain form exists as the performance baseline. */
+PF_API pf_status pf_set_fitness_variant(pf_volume* vol, int variant);
+
+PF_API const char* pf_status_string(pf_status status);
+
+/* --- instrumentation ---------------------------------------------------- */
+
+/* Number of kernels this library has enqueued since it was loaded. */
+PF_API unsigned long long pf_launch_count(void);
+
+/* When enabled, every launch of the named kernel class ("fitness": the
+ * search and pf_fitness launches; "fitness1": the single-pose evaluation of
+ * the mean update; "integrate", "backproject", "raycast") is bracketed by
+ * CUDA events on its stream.  pf_kernel_timing synchronises those events, returns the summed
+ * device time (ms) and launch count since the last query, and clears them. */
+PF_API pf_status pf_set_kernel_timing(int enable);
+PF_API pf_status pf_kernel_timing(const char* kernel_class, double* total_ms, long long* launches);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PROFUSION_H */

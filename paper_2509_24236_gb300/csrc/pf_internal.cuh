@@ -1,0 +1,139 @@
+// Internal declarations shared by the translation units of libprofusion.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <atomic>
+#include <cmath>
+
+#include "../../include/profusion.h"
+
+// --------------------------------------------------------------------------
+// TSDF value encoding in the f32 tsdf array.
+//
+// A node is usable by the fitness when it is observed and within the
+// truncation band (|tsdf| < 1).  Storing the other nodes as non-finite
+// values makes that test fall out of the interpolation itself: a linear
+// interpolation with a NaN or infinite end point is never finite, so the
+// trilinear value of a cell is finite exactly when all eight nodes are
+// usable.  Encoding:
+//   unobserved (weight 0)        -> quiet NaN
+//   observed, tsdf == +1 / -1    -> +inf / -inf
+//   observed, |tsdf| < 1         -> the value
+// --------------------------------------------------------------------------
+#define PF_UNOBSERVED __int_as_float(0x7fc00000)
+
+__host__ __device__ inline float pf_encode(float t, float w)
+{
+#ifdef __CUDA_ARCH__
+    if (!(w > 0.0f)) return __int_as_float(0x7fc00000);
+    if (t >= 1.0f) return __int_as_float(0x7f800000);
+    if (t <= -1.0f) return __int_as_float(0xff800000);
+    return t;
+#else
+    if (!(w > 0.0f)) return NAN;
+    if (t >= 1.0f) return INFINITY;
+    if (t <= -1.0f) return -INFINITY;
+    return t;
+#endif
+}
+
+// Value of an observed node (weight > 0): infinities stand for +-1.
+__host__ __device__ inline float pf_decode(float e)
+{
+    return isinf(e) ? copysignf(1.0f, e) : e;
+}
+
+// --------------------------------------------------------------------------
+// Volume and workspace
+// --------------------------------------------------------------------------
+struct pf_workspace {
+    int pix_cap = 0;        // max pixels per frame
+    int k_cap = 0;          // max particles
+    int part_cap = 0;       // partial slots (tiles x particles)
+    float4* points = nullptr;        // pix_cap
+    int* block_counts = nullptr;     // back-projection blocks
+    int* n_points = nullptr;         // 1
+    float* part_S = nullptr;         // part_cap
+    int* part_C = nullptr;           // part_cap
+    unsigned int* counter = nullptr; // last-block tickets (zeroed, reset by the last block)
+    double* state = nullptr;         // search state, see track.cu
+    double* pose_in = nullptr;       // 16 (sync entry point)
+    double* pose_out = nullptr;      // 16
+    pf_track_stats* stats = nullptr; // 1
+};
+
+struct pf_volume {
+    pf_volume_desc desc;
+    int device = 0;
+    size_t n_nodes = 0;
+    float* tsdf = nullptr;    // encoded, see above
+    float* weight = nullptr;
+    int fitness_variant = 0;
+    pf_workspace ws;
+};
+
+// --------------------------------------------------------------------------
+// Host helpers
+// --------------------------------------------------------------------------
+namespace pf {
+
+extern std::atomic<unsigned long long> g_launches;
+
+inline void count_launch(unsigned n = 1) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+
+enum KernelClass { KC_FITNESS = 0, KC_FITNESS1, KC_INTEGRATE, KC_BACKPROJECT, KC_RAYCAST, KC_COUNT };
+
+// Event bracketing of launches (no-ops unless timing is enabled).
+void timing_begin(KernelClass kc, cudaStream_t s);
+void timing_end(KernelClass kc, cudaStream_t s);
+
+pf_status check_intrinsics(const pf_intrinsics* intr);
+pf_status workspace_reserve(pf_volume* vol, int max_pixels, int k_max);
+
+inline pf_status cuda_status(cudaError_t e)
+{
+    if (e == cudaSuccess) return PF_OK;
+    if (e == cudaErrorMemoryAllocation) return PF_ERR_OOM;
+    return PF_ERR_CUDA;
+}
+
+}  // namespace pf
+
+#define PF_CUDA(call)                                   \
+    do {                                                \
+        cudaError_t e_ = (call);                        \
+        if (e_ != cudaSuccess) return pf::cuda_status(e_); \
+    } while (0)
+
+#define PF_LAUNCHED()                                   \
+    do {                                                \
+        cudaError_t e_ = cudaGetLastError();            \
+        if (e_ != cudaSuccess) return pf::cuda_status(e_); \
+    } while (0)
+
+// Camera parameters in the form the kernels use.
+struct CamK {
+    int width, height;
+    float fx, fy, cx, cy, dmin, dmax;
+};
+
+inline CamK make_cam(const pf_intrinsics* in)
+{
+    CamK c;
+    c.width = in->width;
+    c.height = in->height;
+    c.fx = in->fx;
+    c.fy = in->fy;
+    c.cx = in->cx;
+    c.cy = in->cy;
+    c.dmin = in->depth_min;
+    c.dmax = in->depth_max;
+    return c;
+}
+
+__device__ inline bool pf_depth_usable(float z, float dmin, float dmax)
+{
+    return isfinite(z) && z >= dmin && z <= dmax;
+}

@@ -1,0 +1,342 @@
+// Volume lifetime, host transfer and projective TSDF fusion.
+//
+// Fusion follows the KinectFusion rule the paper adopts (Sec. III, "Method
+// overview"): each node is transformed into the camera, projected to its
+// nearest pixel, and, when that pixel has a usable depth d and the node lies
+// no deeper than one truncation behind it, the truncated z-distance
+// t = min(1, (d - z_c) / tau) enters a running average with weight 1.
+//
+// GB300 layout: one CTA per 32 x 8 x 8 tile of nodes (x fastest, so a warp
+// touches one 128-byte line of each array per slice); the tile is dropped
+// before any memory access when its bounding sphere lies outside the view
+// frustum or beyond depth_max + tau.  Node loads and stores happen only for
+// nodes that pass every test, so HBM traffic is proportional to the nodes
+// actually updated.  The camera-frame depth of a node is formed as a
+// double-precision tile base (split into a float pair) plus a small float
+// offset, which keeps the signed distance accurate to ~1e-7 m at any
+// distance from the grid origin.
+#include <stdlib.h>
+#include <string.h>
+
+#include <vector>
+
+#include "pf_internal.cuh"
+
+namespace {
+
+constexpr int TX = 32, TY = 8, TZ = 8;
+
+struct IntegArgs {
+    float* tsdf;
+    float* weight;
+    int nx, ny, nz;
+    float trunc;
+    float max_weight;
+    CamK cam;
+    const float* depth;
+    const double* pose_dev;             // camera-to-world pose in device memory, or null: use pose
+    double pose[12];                    // row-major 3x4
+    double origin[3];
+    double vs;
+    float plane[4][3];                  // inward normals of the four side planes of the frustum
+    float zfar;                         // nodes deeper than this are never updated
+    float radius;                       // bounding radius of a tile (+ margin)
+};
+
+__global__ void __launch_bounds__(TX * TY) integrate_kernel(IntegArgs a)
+{
+    __shared__ float s_base[4];
+    __shared__ float s_step[9];
+    __shared__ int s_skip;
+    const int i0 = blockIdx.x * TX, j0 = blockIdx.y * TY, k0 = blockIdx.z * TZ;
+    if (threadIdx.x == 0 && threadIdx.y == 0) {
+        // X_c = R^T (X_w - t) with X_w = origin + vs (i, j, k), in FP64 for
+        // the tile's first node; steps per index are vs * (rows of R)
+        const double* P = a.pose_dev ? a.pose_dev : a.pose;
+        double Pl[12];
+        for (int q = 0; q < 12; ++q) Pl[q] = P[q];
+        const double Xw[3] = {a.origin[0] + a.vs * i0, a.origin[1] + a.vs * j0, a.origin[2] + a.vs * k0};
+        const double d[3] = {Xw[0] - Pl[3], Xw[1] - Pl[7], Xw[2] - Pl[11]};
+        double b[3], c[3], st[9];
+        for (int r = 0; r < 3; ++r) {
+            b[r] = Pl[r] * d[0] + Pl[4 + r] * d[1] + Pl[8 + r] * d[2];
+            st[r] = a.vs * Pl[r];          // step along i
+            st[3 + r] = a.vs * Pl[4 + r];  // step along j
+            st[6 + r] = a.vs * Pl[8 + r];  // step along k
+            c[r] = b[r] + 0.5 * (TX - 1) * st[r] + 0.5 * (TY - 1) * st[3 + r] + 0.5 * (TZ - 1) * st[6 + r];
+        }
+        for (int q = 0; q < 9; ++q) s_step[q] = (float)st[q];
+        float hi = (float)b[2];
+        s_base[0] = (float)b[0];
+        s_base[1] = (float)b[1];
+        s_base[2] = hi;
+        s_base[3] = (float)(b[2] - (double)hi);
+        float cx = (float)c[0], cy = (float)c[1], cz = (float)c[2];
+        int skip = (cz + a.radius <= 0.0f) || (cz - a.radius > a.zfar);
+        for (int p = 0; p < 4 && !skip; ++p) {
+            float d = a.plane[p][0] * cx + a.plane[p][1] * cy + a.plane[p][2] * cz;
+            if (d < -a.radius) skip = 1;
+        }
+        s_skip = skip;
+    }
+    __syncthreads();
+    if (s_skip) return;
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int i = i0 + tx, j = j0 + ty;
+    if (i >= a.nx || j >= a.ny) return;
+    const float bx = s_base[0], by = s_base[1], bz_hi = s_base[2], bz_lo = s_base[3];
+    const float ai[3] = {s_step[0], s_step[1], s_step[2]};
+    const float aj[3] = {s_step[3], s_step[4], s_step[5]};
+    const float ak[3] = {s_step[6], s_step[7], s_step[8]};
+    const float lx = fmaf((float)tx, ai[0], (float)ty * aj[0]);
+    const float ly = fmaf((float)tx, ai[1], (float)ty * aj[1]);
+    const float lz = fmaf((float)tx, ai[2], (float)ty * aj[2]);
+    const size_t plane_stride = (size_t)a.nx * a.ny;
+    size_t idx = (size_t)i + (size_t)a.nx * j + plane_stride * k0;
+    for (int dz = 0; dz < TZ; ++dz, idx += plane_stride) {
+        const int k = k0 + dz;
+        if (k >= a.nz) break;
+        const float fz = (float)dz;
+        const float xc = bx + fmaf(fz, ak[0], lx);
+        const float yc = by + fmaf(fz, ak[1], ly);
+        const float zl = bz_lo + fmaf(fz, ak[2], lz);
+        const float zc = bz_hi + zl;
+        if (!(zc > 0.0f)) continue;
+        const float inv = __frcp_rn(zc);
+        const float u = fmaf(a.cam.fx * xc, inv, a.cam.cx);
+        const float v = fmaf(a.cam.fy * yc, inv, a.cam.cy);
+        const float uf = floorf(u + 0.5f), vf = floorf(v + 0.5f);
+        if (!(uf >= 0.0f && uf < (float)a.cam.width && vf >= 0.0f && vf < (float)a.cam.height)) continue;
+        const float d = __ldg(a.depth + (size_t)vf * a.cam.width + (size_t)uf);
+        if (!pf_depth_usable(d, a.cam.dmin, a.cam.dmax)) continue;
+        const float sdf = (d - bz_hi) - zl;
+        if (sdf < -a.trunc) continue;
+        const float t = fminf(1.0f, __fdiv_rn(sdf, a.trunc));
+        const float w = a.weight[idx];
+        float tn = t;
+        if (w > 0.0f) tn = __fdiv_rn(fmaf(w, pf_decode(a.tsdf[idx]), t), w + 1.0f);
+        const float wn = fminf(w + 1.0f, a.max_weight);
+        a.tsdf[idx] = pf_encode(tn, wn);
+        a.weight[idx] = wn;
+    }
+}
+
+__global__ void fill_kernel(float* tsdf, float* weight, size_t n)
+{
+    size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+    size_t step = (size_t)gridDim.x * blockDim.x;
+    for (; i < n; i += step) {
+        tsdf[i] = PF_UNOBSERVED;
+        weight[i] = 0.0f;
+    }
+}
+
+pf_status check_desc(const pf_volume_desc* d)
+{
+    if (!d) return PF_ERR_INVALID_ARG;
+    if (d->nx < 2 || d->ny < 2 || d->nz < 2 || d->nx > 4096 || d->ny > 4096 || d->nz > 4096)
+        return PF_ERR_INVALID_ARG;
+    if ((double)d->nx * d->ny * d->nz >= 2147483648.0) return PF_ERR_INVALID_ARG;
+    if (!(d->voxel_size > 0.0f) || !(d->trunc > 0.0f) || !std::isfinite(d->voxel_size) || !std::isfinite(d->trunc))
+        return PF_ERR_INVALID_ARG;
+    for (int a = 0; a < 3; ++a)
+        if (!std::isfinite(d->origin[a])) return PF_ERR_INVALID_ARG;
+    if (d->max_weight < 1 || d->max_weight > 65535) return PF_ERR_INVALID_ARG;
+    if (d->tsdf_dtype != PF_F32 || d->weight_u8 != 0) return PF_ERR_UNSUPPORTED;
+    return PF_OK;
+}
+
+pf_status enqueue_reset(pf_volume* v, cudaStream_t s)
+{
+    int blocks = 152 * 8;
+    fill_kernel<<<blocks, 256, 0, s>>>(v->tsdf, v->weight, v->n_nodes);
+    pf::count_launch();
+    PF_LAUNCHED();
+    return PF_OK;
+}
+
+bool finite_pose(const double* P)
+{
+    for (int i = 0; i < 12; ++i)
+        if (!std::isfinite(P[i])) return false;
+    return true;
+}
+
+}  // namespace
+
+extern "C" {
+
+pf_status pf_create_volume(const pf_volume_desc* desc, void* stream, pf_volume** out)
+{
+    if (!out) return PF_ERR_INVALID_ARG;
+    *out = nullptr;
+    pf_status st = check_desc(desc);
+    if (st != PF_OK) return st;
+    pf_volume* v = new pf_volume();
+    v->desc = *desc;
+    v->n_nodes = (size_t)desc->nx * desc->ny * desc->nz;
+    cudaError_t e = cudaGetDevice(&v->device);
+    if (e == cudaSuccess) e = cudaMalloc(&v->tsdf, v->n_nodes * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc(&v->weight, v->n_nodes * sizeof(float));
+    if (e != cudaSuccess) {
+        cudaFree(v->tsdf);
+        cudaFree(v->weight);
+        delete v;
+        cudaGetLastError();
+        return pf::cuda_status(e);
+    }
+    st = enqueue_reset(v, (cudaStream_t)stream);
+    if (st != PF_OK) {
+        pf_destroy_volume(v);
+        return st;
+    }
+    *out = v;
+    return PF_OK;
+}
+
+pf_status pf_destroy_volume(pf_volume* v)
+{
+    if (!v) return PF_OK;
+    cudaDeviceSynchronize();
+    cudaFree(v->tsdf);
+    cudaFree(v->weight);
+    pf_workspace& w = v->ws;
+    cudaFree(w.points);
+    cudaFree(w.block_counts);
+    cudaFree(w.n_points);
+    cudaFree(w.part_S);
+    cudaFree(w.part_C);
+    cudaFree(w.counter);
+    cudaFree(w.state);
+    cudaFree(w.pose_in);
+    cudaFree(w.pose_out);
+    cudaFree(w.stats);
+    delete v;
+    return PF_OK;
+}
+
+pf_status pf_reset_volume(pf_volume* v, void* stream)
+{
+    if (!v) return PF_ERR_INVALID_ARG;
+    return enqueue_reset(v, (cudaStream_t)stream);
+}
+
+pf_status pf_set_fitness_variant(pf_volume* v, int variant)
+{
+    if (!v || variant < 0 || variant > 1) return PF_ERR_INVALID_ARG;
+    v->fitness_variant = variant;
+    return PF_OK;
+}
+
+pf_status pf_volume_upload(pf_volume* v, const float* tsdf_host, const float* weight_host)
+{
+    if (!v || !tsdf_host || !weight_host) return PF_ERR_INVALID_ARG;
+    std::vector<float> enc(v->n_nodes);
+    for (size_t i = 0; i < v->n_nodes; ++i) {
+        float w = weight_host[i];
+        if (!(w >= 0.0f) || !std::isfinite(w) || w > (float)v->desc.max_weight) return PF_ERR_INVALID_ARG;
+        if (w > 0.0f && !(std::fabs(tsdf_host[i]) <= 1.0f)) return PF_ERR_INVALID_ARG;
+        enc[i] = pf_encode(tsdf_host[i], w);
+    }
+    PF_CUDA(cudaDeviceSynchronize());
+    PF_CUDA(cudaMemcpy(v->tsdf, enc.data(), v->n_nodes * sizeof(float), cudaMemcpyHostToDevice));
+    PF_CUDA(cudaMemcpy(v->weight, weight_host, v->n_nodes * sizeof(float), cudaMemcpyHostToDevice));
+    return PF_OK;
+}
+
+pf_status pf_volume_download(const pf_volume* v, float* tsdf_host, float* weight_host)
+{
+    if (!v || !tsdf_host || !weight_host) return PF_ERR_INVALID_ARG;
+    PF_CUDA(cudaDeviceSynchronize());
+    PF_CUDA(cudaMemcpy(tsdf_host, v->tsdf, v->n_nodes * sizeof(float), cudaMemcpyDeviceToHost));
+    PF_CUDA(cudaMemcpy(weight_host, v->weight, v->n_nodes * sizeof(float), cudaMemcpyDeviceToHost));
+    for (size_t i = 0; i < v->n_nodes; ++i)
+        tsdf_host[i] = weight_host[i] > 0.0f ? pf_decode(tsdf_host[i]) : 1.0f;
+    return PF_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+pf_status integrate_impl(pf_volume* v, const float* depth_dev, const pf_intrinsics* intr, const double* P_host,
+                         const double* P_dev, cudaStream_t s)
+{
+    if (!v || !depth_dev) return PF_ERR_INVALID_ARG;
+    pf_status st = pf::check_intrinsics(intr);
+    if (st != PF_OK) return st;
+    const pf_volume_desc& d = v->desc;
+    IntegArgs a;
+    a.tsdf = v->tsdf;
+    a.weight = v->weight;
+    a.nx = d.nx;
+    a.ny = d.ny;
+    a.nz = d.nz;
+    a.trunc = d.trunc;
+    a.max_weight = (float)d.max_weight;
+    a.cam = make_cam(intr);
+    a.depth = depth_dev;
+    a.pose_dev = P_dev;
+    for (int q = 0; q < 12; ++q) a.pose[q] = P_host ? P_host[q] : 0.0;
+    for (int q = 0; q < 3; ++q) a.origin[q] = d.origin[q];
+    a.vs = d.voxel_size;
+    // side planes through the camera centre: pixel range u in [-0.5, W - 0.5)
+    const double lx0 = (-0.5 - intr->cx) / intr->fx, lx1 = (intr->width - 0.5 - intr->cx) / intr->fx;
+    const double ly0 = (-0.5 - intr->cy) / intr->fy, ly1 = (intr->height - 0.5 - intr->cy) / intr->fy;
+    const double pl[4][3] = {{1.0, 0.0, -lx0}, {-1.0, 0.0, lx1}, {0.0, 1.0, -ly0}, {0.0, -1.0, ly1}};
+    for (int p = 0; p < 4; ++p) {
+        double n = sqrt(pl[p][0] * pl[p][0] + pl[p][1] * pl[p][1] + pl[p][2] * pl[p][2]);
+        for (int c = 0; c < 3; ++c) a.plane[p][c] = (float)(pl[p][c] / n);
+    }
+    a.zfar = d.trunc + intr->depth_max;
+    const double vs = d.voxel_size;
+    a.radius = (float)(0.5 * vs * sqrt((double)((TX - 1) * (TX - 1) + (TY - 1) * (TY - 1) + (TZ - 1) * (TZ - 1)))
+                       + 0.01 * vs + 1e-3);
+    dim3 grid((d.nx + TX - 1) / TX, (d.ny + TY - 1) / TY, (d.nz + TZ - 1) / TZ);
+    pf::timing_begin(pf::KC_INTEGRATE, s);
+    integrate_kernel<<<grid, dim3(TX, TY), 0, s>>>(a);
+    pf::count_launch();
+    pf::timing_end(pf::KC_INTEGRATE, s);
+    PF_LAUNCHED();
+    return PF_OK;
+}
+
+__global__ void compose_kernel(const double* A, const double* B, double* out)
+{
+    const int t = threadIdx.x;
+    if (t < 16) {
+        const int r = t >> 2, c = t & 3;
+        double acc = 0.0;
+        for (int m = 0; m < 4; ++m) acc += A[4 * r + m] * B[4 * m + c];
+        out[t] = acc;
+    }
+}
+
+}  // namespace
+
+extern "C" {
+
+pf_status pf_integrate(pf_volume* v, const float* depth_dev, const pf_intrinsics* intr, const double P[16],
+                       void* stream)
+{
+    if (!P || !finite_pose(P)) return PF_ERR_INVALID_ARG;
+    return integrate_impl(v, depth_dev, intr, P, nullptr, (cudaStream_t)stream);
+}
+
+pf_status pf_integrate_async(pf_volume* v, const float* depth_dev, const pf_intrinsics* intr,
+                             const double* P_dev, void* stream)
+{
+    if (!P_dev) return PF_ERR_INVALID_ARG;
+    return integrate_impl(v, depth_dev, intr, nullptr, P_dev, (cudaStream_t)stream);
+}
+
+pf_status pf_pose_compose(const double* a_dev, const double* b_dev, double* out_dev, void* stream)
+{
+    if (!a_dev || !b_dev || !out_dev || out_dev == a_dev || out_dev == b_dev) return PF_ERR_INVALID_ARG;
+    compose_kernel<<<1, 32, 0, (cudaStream_t)stream>>>(a_dev, b_dev, out_dev);
+    pf::count_launch();
+    PF_LAUNCHED();
+    return PF_OK;
+}
+
+}  // extern "C"

@@ -7,7 +7,8 @@ random numbers the method consumes (the templates) are produced here and passed
 to both implementations as inputs.
 """
 from .camera import (Intrinsics, add_depth_noise, axis_angle_matrix, look_at, multiroom_trajectory,
-                     perturbation, pose_matrix, relative, render_depth, room_view, yaw_pitch_roll_pose)
+                     perturbation, pose_matrix, relative, render_depth, render_points, room_view,
+                     yaw_pitch_roll_pose)
 from .rng import splitmix64, templates, uniform01
 from .scenes import Primitive, Scene, multiroom_scene, room_scene
 from .volume import Grid, analytic_tsdf

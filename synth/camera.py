@@ -77,6 +77,21 @@ def render_depth(scene, intr: Intrinsics, pose: np.ndarray) -> np.ndarray:
     return depth.astype(np.float32)
 
 
+def render_points(scene, intr: Intrinsics, pose: np.ndarray, stride: int = 1) -> np.ndarray:
+    """Camera-frame hit points (float32, N x 4, last column 0) of the rays
+    of every `stride`-th pixel that hits the scene, in row-major order."""
+    u = np.arange(intr.width, dtype=np.float64)
+    v = np.arange(intr.height, dtype=np.float64)
+    uu, vv = np.meshgrid(u, v)
+    dc = np.stack([(uu - intr.cx) / intr.fx, (vv - intr.cy) / intr.fy, np.ones_like(uu)], axis=-1)
+    lam = scene.intersect(pose[:3, 3], dc @ pose[:3, :3].T)
+    hit = np.isfinite(lam).reshape(-1)
+    pts = (dc * lam[..., None]).reshape(-1, 3)[hit][::stride]
+    out = np.zeros((pts.shape[0], 4), dtype=np.float32)
+    out[:, :3] = pts
+    return out
+
+
 def add_depth_noise(depth: np.ndarray, seed: int, sigma_const: float = 0.0,
                     sigma_quad: float = 0.0) -> np.ndarray:
     """Additive Gaussian noise with sigma = sigma_const + sigma_quad * z^2 on
