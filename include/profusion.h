@@ -227,11 +227,17 @@ PF_API pf_status pf_track_reserve(pf_volume* vol, int max_pixels, int k_max);
 PF_API pf_status pf_raycast(const pf_volume* vol, const pf_intrinsics* intr, const double cam_to_world[16],
                      float* depth_out_dev, float* normal_out_dev_or_null, void* cuda_stream);
 
-/* Fitness kernel variant used by pf_fitness and the search of this volume:
- * 0 (default) reads only the tsdf array, whose encoding makes a cell's
- * validity a property of its interpolated value; 1 is the plain form that
- * also reads the weights and tests all eight nodes explicitly.  Results are
- * identical; the plain form exists as the performance baseline. */
+/* Fitness kernel variant used by pf_fitness and the search of this volume,
+ * variant = layout + 2 * mapping.
+ *   layout  0 (default): reads only the tsdf array, whose encoding makes a
+ *           cell's validity a property of its interpolated value;
+ *           1: the plain form that also reads the weights and tests all
+ *           eight nodes explicitly (the performance baseline).
+ *   mapping 0 (default): chosen per block of points from the spread of the
+ *           particles; 1: neighbouring points on the lanes of a warp;
+ *           2: particles on the lanes of a warp.
+ * All variants evaluate the same samples: counts are identical and fitness
+ * values differ only by the float summation order. */
 PF_API pf_status pf_set_fitness_variant(pf_volume* vol, int variant);
 
 PF_API const char* pf_status_string(pf_status status);

@@ -77,7 +77,7 @@ def _load():
         lib.or_sample.argtypes = [dp, dp, C.POINTER(_Grid), dp, dp]
         lib.or_fitness.restype = None
         lib.or_fitness.argtypes = [dp, dp, C.POINTER(_Grid), dp, C.c_long, C.c_long, dp, C.c_int,
-                                   dp, lp, dp, lp, C.c_double]
+                                   dp, lp, dp, lp, C.c_double, dp, C.c_int]
         lib.or_sample_band.restype = C.c_int
         lib.or_sample_band.argtypes = [dp, dp, C.POINTER(_Grid), dp, dp]
         lib.or_so3_exp.restype = None
@@ -164,12 +164,17 @@ class FitnessResult:
     S: np.ndarray
     C: np.ndarray
     E: np.ndarray
-    amb: np.ndarray | None
+    amb: np.ndarray | None = None    # ambiguous points per pose (excluded from S, C)
+    vals: np.ndarray | None = None   # their values when counted, K x cap
 
 
 def fitness(vol: Volume, points, poses, stride: int = 1, ambiguity: bool = False,
-            eps_g: float = 2e-4) -> FitnessResult:
-    """E_k for K row-major 3x4 poses (K x 12) against points (N x 3)."""
+            eps_g: float = 1e-4, cap: int = 32) -> FitnessResult:
+    """E_k for K row-major 3x4 poses (K x 12) against points (N x 3).
+
+    With ambiguity=True, points within eps_g voxels of a cell face across
+    which validity changes are left out of S, C, E and reported instead
+    (count per pose in `amb`, their values in `vals`)."""
     pts = _f64(np.asarray(points)[:, :3])
     T = _f64(np.asarray(poses).reshape(-1, 12))
     K = T.shape[0]
@@ -177,11 +182,13 @@ def fitness(vol: Volume, points, poses, stride: int = 1, ambiguity: bool = False
     Cn = np.empty(K, dtype=np.int64)
     E = np.empty(K)
     A = np.empty(K, dtype=np.int64) if ambiguity else None
+    V = np.zeros((K, cap)) if ambiguity else None
     _load().or_fitness(_p(vol.tsdf, C.c_double), _p(vol.weight, C.c_double), C.byref(vol._g()),
                        _p(pts, C.c_double), pts.shape[0], int(stride), _p(T, C.c_double), K,
                        _p(S, C.c_double), _p(Cn, C.c_long), _p(E, C.c_double),
-                       _p(A, C.c_long) if A is not None else None, eps_g)
-    return FitnessResult(S, Cn, E, A)
+                       _p(A, C.c_long) if A is not None else None, eps_g,
+                       _p(V, C.c_double) if V is not None else None, cap)
+    return FitnessResult(S, Cn, E, A, V)
 
 
 def so3_exp(w) -> np.ndarray:

@@ -183,36 +183,61 @@ static void transform(const double T[12], const double x[3], double q[3])
 }
 
 /* One pose against points (every `stride`-th of n).  S = sum |tsdf|,
- * C = |X|.  If amb != NULL, counts points lying within eps_g voxels of a cell
- * face across which cell validity changes, i.e. whose membership in X could
- * flip under a perturbation of that size (test aid). */
+ * C = |X|.  Test aid: when amb != NULL, a point lying within eps_g voxels of
+ * a cell face across which cell validity changes (its membership in X could
+ * flip under a perturbation of that size) is counted in *amb instead of S, C
+ * -- S and C then cover the unambiguous points only -- and the value it
+ * contributes when counted as valid (its |tsdf| in the valid cell) is
+ * written to vals[0 .. cap). */
 static void fitness_one(const double* tsdf, const double* weight, const or_grid* g,
                         const double* pts, long n, long stride, const double T[12],
-                        double* S, long* C, long* amb, double eps_g)
+                        double* S, long* C, long* amb, double eps_g, double* vals, int cap)
 {
     double s = 0.0;
     long c = 0, a = 0;
     for (long j = 0; j < n; j += stride) {
         double q[3], t, gc[3];
         transform(T, pts + 3 * j, q);
-        if (sample_cell(tsdf, weight, g, q, 1, &t, gc)) {
-            s += fabs(t);
-            c += 1;
-        }
+        int ok = sample_cell(tsdf, weight, g, q, 1, &t, gc);
         if (amb) {
             long i0[3];
             for (int ax = 0; ax < 3; ++ax) i0[ax] = (long)floor(gc[ax]);
             int here = cell_ok(tsdf, weight, g, i0[0], i0[1], i0[2]);
             int flag = 0;
+            long alt[3] = {i0[0], i0[1], i0[2]};
             for (int ax = 0; ax < 3 && !flag; ++ax) {
                 double fr = gc[ax] - floor(gc[ax]);
-                long alt[3] = {i0[0], i0[1], i0[2]};
+                alt[0] = i0[0];
+                alt[1] = i0[1];
+                alt[2] = i0[2];
                 if (fr < eps_g) alt[ax] -= 1;
                 else if (fr > 1.0 - eps_g) alt[ax] += 1;
                 else continue;
                 if (cell_ok(tsdf, weight, g, alt[0], alt[1], alt[2]) != here) flag = 1;
             }
-            a += flag;
+            if (flag) {
+                double v = 0.0;
+                if (ok) {
+                    v = fabs(t);
+                } else {
+                    /* the value in the neighbouring valid cell, at the face */
+                    double qa[3];
+                    for (int ax = 0; ax < 3; ++ax) {
+                        double lo = (double)alt[ax], hi = lo + 1.0;
+                        double gg = gc[ax] < lo ? lo : (gc[ax] > hi ? hi - 1e-12 : gc[ax]);
+                        qa[ax] = g->origin[ax] + gg * g->voxel_size;
+                    }
+                    double ta;
+                    if (sample_cell(tsdf, weight, g, qa, 1, &ta, 0)) v = fabs(ta);
+                }
+                if (a < cap) vals[a] = v;
+                ++a;
+                continue;
+            }
+        }
+        if (ok) {
+            s += fabs(t);
+            c += 1;
         }
     }
     *S = s;
@@ -221,16 +246,18 @@ static void fitness_one(const double* tsdf, const double* weight, const or_grid*
 }
 
 /* K poses (row-major 3x4) against the points: S_k, C_k, E_k (= +inf when
- * C_k = 0, reading: an empty valid set never improves the fit). */
+ * C_k = 0, reading: an empty valid set never improves the fit).  With amb,
+ * see fitness_one: vals holds cap values per pose. */
 void or_fitness(const double* tsdf, const double* weight, const or_grid* g,
                 const double* pts, long n, long stride, const double* poses, int K,
-                double* S, long* C, double* E, long* amb, double eps_g)
+                double* S, long* C, double* E, long* amb, double eps_g, double* vals, int cap)
 {
 #pragma omp parallel for schedule(dynamic, 1)
     for (int k = 0; k < K; ++k) {
         double s;
         long c, a = 0;
-        fitness_one(tsdf, weight, g, pts, n, stride, poses + 12 * k, &s, &c, amb ? &a : 0, eps_g);
+        fitness_one(tsdf, weight, g, pts, n, stride, poses + 12 * k, &s, &c, amb ? &a : 0, eps_g,
+                    vals ? vals + (size_t)k * cap : 0, cap);
         S[k] = s;
         C[k] = c;
         E[k] = c > 0 ? s / (double)c : INFINITY;
@@ -362,7 +389,7 @@ int or_track(const double* tsdf, const double* weight, const or_grid* g,
 
         /* sample delta poses within s and form dP_k * P (particle 0 is P) */
         or_particles(templ, K, P, s_deg, s_cm, prm->compose_mode, T);
-        or_fitness(tsdf, weight, g, pts, n, stride, T, K, S, C, E, 0, 0.0);
+        or_fitness(tsdf, weight, g, pts, n, stride, T, K, S, C, E, 0, 0.0, 0, 0);
 
         /* best particle: smallest E, lowest index among equals */
         int kb = 0;
@@ -420,7 +447,7 @@ int or_track(const double* tsdf, const double* weight, const or_grid* g,
                 orthonormalise(Pn);
                 double s1, e1;
                 long c1;
-                or_fitness(tsdf, weight, g, pts, n, stride, Pn, 1, &s1, &c1, &e1, 0, 0.0);
+                or_fitness(tsdf, weight, g, pts, n, stride, Pn, 1, &s1, &c1, &e1, 0, 0.0, 0, 0);
                 E_new = e1;
             } else {
                 memcpy(Pn, P, sizeof(Pn));

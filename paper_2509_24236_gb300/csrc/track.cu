@@ -170,6 +170,7 @@ struct FitArgs {
     int stride;           // evaluate points 0, stride, 2*stride, ...
     int K;                // particles of this launch
     const float* poses;   // SRC_POSES: K x 12
+    float pm_threshold;   // particles on lanes when the chunk's spread (voxels) is below this
     const float* templ;   // SRC_SEARCH: templates, row k = particle k
     SearchState* st;
     int compose_mode, update_mode;
@@ -192,34 +193,6 @@ struct FitArgs {
     pf_track_stats* stats;
     int iter;
 };
-
-// Rotation matrix of a rotation vector in float (particles only; the pose
-// update uses the double version below).  1 - cos is formed as 2 sin^2(h/2)
-// to avoid cancellation.
-__device__ inline void so3_exp_f(float wx, float wy, float wz, float R[9])
-{
-    const float th2 = wx * wx + wy * wy + wz * wz;
-    const float th = sqrtf(th2);
-    float a, b;
-    if (th < 1e-6f) {
-        a = 1.0f;
-        b = 0.5f;
-    } else {
-        float sh, ch;
-        sincosf(0.5f * th, &sh, &ch);
-        a = 2.0f * sh * ch / th;
-        b = 2.0f * sh * sh / th2;
-    }
-    R[0] = 1.0f - b * (wy * wy + wz * wz);
-    R[1] = -a * wz + b * wx * wy;
-    R[2] = a * wy + b * wx * wz;
-    R[3] = a * wz + b * wx * wy;
-    R[4] = 1.0f - b * (wx * wx + wz * wz);
-    R[5] = -a * wx + b * wy * wz;
-    R[6] = -a * wy + b * wx * wz;
-    R[7] = a * wx + b * wy * wz;
-    R[8] = 1.0f - b * (wx * wx + wy * wy);
-}
 
 __device__ inline void so3_exp_d(const double w[3], double R[9])
 {
@@ -269,32 +242,102 @@ __device__ inline void compose_d(const double dR[9], const double dt[3], const d
         }
 }
 
-// World transform (float 3x4) -> grid-unit transform g = A x + b.
-__device__ inline void to_grid(const float* Rw, const float* tw, double inv_vs, const double org[3], float* T)
+// A particle as the sampling loop uses it.  g = (A_hi + A_lo) x + b maps a
+// camera-frame point to grid units relative to an integer cell offset o: the
+// grid coordinate is g + o.  A = R / voxel carried as a float pair and
+// |b| < 1 make the transform as accurate as the FP64 pose it came from (the
+// rounding of a single float matrix would shift every point of a particle
+// the same way); the offset is folded into the cell bounds [lo, hi) and into
+// the magic constant of the floor, so it costs nothing per sample.
+struct Particle {      // shared memory, 128 bytes
+    float4 h0, h1, h2; // rows of A_hi | b
+    float4 l0, l1, l2; // rows of A_lo | lo bound
+    float4 u;          // hi bounds x y z | magic x
+    float4 m;          // magic y z | translation, rotation distance to the chunk's first particle
+};
+
+struct Xform {         // the same in registers
+    float a[9], l[9], b[3], lo[3], hi[3];
+    int mg[3];
+};
+
+constexpr int kMagicBits = 0x4b400000;  // bits of 1.5 * 2^23
+
+// Grid-unit particle from a camera-to-world pose [R | t] given in FP64.
+__device__ inline void make_particle(const double R[9], const double t[3], const FitArgs& a, Particle& P)
 {
-    const float s = (float)inv_vs;
+    const double iv = 1.0 / a.vs;
+    const int n[3] = {a.nx, a.ny, a.nz};
+    float hi_[3][4], lo_[3][3], lob[3], hib[3];
+    int magic[3];
+    bool ok = true;
     for (int r = 0; r < 3; ++r) {
-        T[4 * r + 0] = Rw[3 * r + 0] * s;
-        T[4 * r + 1] = Rw[3 * r + 1] * s;
-        T[4 * r + 2] = Rw[3 * r + 2] * s;
-        T[4 * r + 3] = (tw[r] - (float)org[r]) * s;
+        const double tg = (t[r] - a.org[r]) * iv;
+        ok = ok && fabs(tg) < 2097152.0;  // 2^21: beyond, no point can reach the grid
+        const double o = ok ? floor(tg) : 0.0;
+        for (int c = 0; c < 3; ++c) {
+            const double Ag = R[3 * r + c] * iv;
+            const float h = (float)Ag;
+            hi_[r][c] = h;
+            lo_[r][c] = (float)(Ag - (double)h);
+        }
+        hi_[r][3] = (float)(tg - o);
+        lob[r] = (float)(-o);
+        hib[r] = (float)((double)(n[r] - 1) - o);
+        magic[r] = kMagicBits - (int)o;
     }
+    if (!ok)
+        for (int r = 0; r < 3; ++r) {
+            lob[r] = 1.0f;
+            hib[r] = 0.0f;
+        }
+    P.h0 = make_float4(hi_[0][0], hi_[0][1], hi_[0][2], hi_[0][3]);
+    P.h1 = make_float4(hi_[1][0], hi_[1][1], hi_[1][2], hi_[1][3]);
+    P.h2 = make_float4(hi_[2][0], hi_[2][1], hi_[2][2], hi_[2][3]);
+    P.l0 = make_float4(lo_[0][0], lo_[0][1], lo_[0][2], lob[0]);
+    P.l1 = make_float4(lo_[1][0], lo_[1][1], lo_[1][2], lob[1]);
+    P.l2 = make_float4(lo_[2][0], lo_[2][1], lo_[2][2], lob[2]);
+    P.u = make_float4(hib[0], hib[1], hib[2], __int_as_float(magic[0]));
+    P.m = make_float4(__int_as_float(magic[1]), __int_as_float(magic[2]), 0.0f, 0.0f);
+}
+
+__device__ __forceinline__ void load_xform(const Particle& P, Xform& X)
+{
+    const float4 h0 = P.h0, h1 = P.h1, h2 = P.h2, l0 = P.l0, l1 = P.l1, l2 = P.l2, u = P.u, m = P.m;
+    X.a[0] = h0.x; X.a[1] = h0.y; X.a[2] = h0.z; X.b[0] = h0.w;
+    X.a[3] = h1.x; X.a[4] = h1.y; X.a[5] = h1.z; X.b[1] = h1.w;
+    X.a[6] = h2.x; X.a[7] = h2.y; X.a[8] = h2.z; X.b[2] = h2.w;
+    X.l[0] = l0.x; X.l[1] = l0.y; X.l[2] = l0.z; X.lo[0] = l0.w;
+    X.l[3] = l1.x; X.l[4] = l1.y; X.l[5] = l1.z; X.lo[1] = l1.w;
+    X.l[6] = l2.x; X.l[7] = l2.y; X.l[8] = l2.z; X.lo[2] = l2.w;
+    X.hi[0] = u.x; X.hi[1] = u.y; X.hi[2] = u.z; X.mg[0] = __float_as_int(u.w);
+    X.mg[1] = __float_as_int(m.x); X.mg[2] = __float_as_int(m.y);
+}
+
+// Grid coordinates (relative to the particle's cell offset) of a point:
+// the small A_lo terms and b first, then A_hi.
+__device__ __forceinline__ void apply(const Xform& X, float x, float y, float z, float& gx, float& gy, float& gz)
+{
+    gx = fmaf(X.a[0], x, fmaf(X.a[1], y, fmaf(X.a[2], z, fmaf(X.l[0], x, fmaf(X.l[1], y, fmaf(X.l[2], z, X.b[0]))))));
+    gy = fmaf(X.a[3], x, fmaf(X.a[4], y, fmaf(X.a[5], z, fmaf(X.l[3], x, fmaf(X.l[4], y, fmaf(X.l[5], z, X.b[1]))))));
+    gz = fmaf(X.a[6], x, fmaf(X.a[7], y, fmaf(X.a[8], z, fmaf(X.l[6], x, fmaf(X.l[7], y, fmaf(X.l[8], z, X.b[2]))))));
 }
 
 // Fast-path sample: tsdf only.  Non-finite nodes (unobserved or outside the
 // band) make the interpolated value non-finite, so the validity test of the
 // cell is a single comparison on the result.
-__device__ __forceinline__ void sample_encoded(const float* __restrict__ tsdf, int nx, int nxy, float gmx, float gmy,
-                                               float gmz, float gx, float gy, float gz, float& s, int& c)
+__device__ __forceinline__ void sample_encoded(const float* __restrict__ tsdf, int nx, int nxy, const Xform& X,
+                                               float gx, float gy, float gz, float& s, int& c)
 {
-    if (gx >= 0.0f && gx < gmx && gy >= 0.0f && gy < gmy && gz >= 0.0f && gz < gmz) {
-        // floor(g) for 0 <= g < 2^22: adding 1.5*2^23 rounding down leaves
-        // floor(g) in the low mantissa bits and keeps every step exact
+    if (gx >= X.lo[0] && gx < X.hi[0] && gy >= X.lo[1] && gy < X.hi[1] && gz >= X.lo[2] && gz < X.hi[2]) {
+        // floor(g) for |g| < 2^22: adding 1.5*2^23 rounding down leaves
+        // floor(g) in the low mantissa bits and keeps every step exact; the
+        // particle's magic constant also adds its integer cell offset
         const float M = 12582912.0f;
         const float rx = __fadd_rd(gx, M), ry = __fadd_rd(gy, M), rz = __fadd_rd(gz, M);
-        const int ix = __float_as_int(rx) & 0x3fffff;
-        const int iy = __float_as_int(ry) & 0x3fffff;
-        const int iz = __float_as_int(rz) & 0x3fffff;
+        const int ix = __float_as_int(rx) - X.mg[0];
+        const int iy = __float_as_int(ry) - X.mg[1];
+        const int iz = __float_as_int(rz) - X.mg[2];
         const float fx = gx - (rx - M), fy = gy - (ry - M), fz = gz - (rz - M);
         const float* p = tsdf + (ix + nx * iy + nxy * iz);
         const float v000 = __ldg(p), v100 = __ldg(p + 1);
@@ -317,13 +360,14 @@ __device__ __forceinline__ void sample_encoded(const float* __restrict__ tsdf, i
 
 // Plain sample: tsdf and weight, all eight nodes tested explicitly.
 __device__ __forceinline__ void sample_plain(const float* __restrict__ tsdf, const float* __restrict__ weight, int nx,
-                                             int nxy, float gmx, float gmy, float gmz, float gx, float gy, float gz,
-                                             float& s, int& c)
+                                             int nxy, const Xform& X, float gx, float gy, float gz, float& s, int& c)
 {
-    if (gx >= 0.0f && gx < gmx && gy >= 0.0f && gy < gmy && gz >= 0.0f && gz < gmz) {
-        const float fx0 = floorf(gx), fy0 = floorf(gy), fz0 = floorf(gz);
-        const int base = (int)fx0 + nx * (int)fy0 + nxy * (int)fz0;
-        const float fx = gx - fx0, fy = gy - fy0, fz = gz - fz0;
+    if (gx >= X.lo[0] && gx < X.hi[0] && gy >= X.lo[1] && gy < X.hi[1] && gz >= X.lo[2] && gz < X.hi[2]) {
+        const float M = 12582912.0f;
+        const float rx = __fadd_rd(gx, M), ry = __fadd_rd(gy, M), rz = __fadd_rd(gz, M);
+        const int base = (__float_as_int(rx) - X.mg[0]) + nx * (__float_as_int(ry) - X.mg[1]) +
+                         nxy * (__float_as_int(rz) - X.mg[2]);
+        const float fx = gx - (rx - M), fy = gy - (ry - M), fz = gz - (rz - M);
         const int off[8] = {0, 1, nx, nx + 1, nxy, nxy + 1, nxy + nx, nxy + nx + 1};
         float v[8];
         bool ok = true;
@@ -346,47 +390,56 @@ __device__ __forceinline__ void sample_plain(const float* __restrict__ tsdf, con
     }
 }
 
+template <int VARIANT>
+__device__ __forceinline__ void sample(const FitArgs& a, int nx, int nxy, const Xform& X, float x, float y, float z,
+                                       float& s, int& c)
+{
+    float gx, gy, gz;
+    apply(X, x, y, z, gx, gy, gz);
+    if (VARIANT == 0)
+        sample_encoded(a.tsdf, nx, nxy, X, gx, gy, gz, s, c);
+    else
+        sample_plain(a.tsdf, a.weight, nx, nxy, X, gx, gy, gz, s, c);
+}
+
+// Particles k_begin .. k_begin+kc-1 of this launch into shared memory, in FP64
+// (the search composes dP_k * P exactly as the pose update does).
 template <int SRC>
-__device__ void build_transforms(const FitArgs& a, int k_begin, int kc, float (*sT)[12])
+__device__ void build_particles(const FitArgs& a, int k_begin, int kc, Particle* sP)
 {
     const int t = threadIdx.x;
     if (t >= kc) return;
     const int k = k_begin + t;
-    float Rw[9], tw[3];
+    double R[9], tw[3];
     if (SRC == SRC_POSES) {
         const float* p = a.poses + 12 * (size_t)k;
         for (int r = 0; r < 3; ++r) {
-            Rw[3 * r + 0] = p[4 * r + 0];
-            Rw[3 * r + 1] = p[4 * r + 1];
-            Rw[3 * r + 2] = p[4 * r + 2];
-            tw[r] = p[4 * r + 3];
+            for (int c = 0; c < 3; ++c) R[3 * r + c] = (double)p[4 * r + c];
+            tw[r] = (double)p[4 * r + 3];
         }
     } else {
-        const SearchState* st = a.st;
-        float R[9], tp[3];
-        for (int r = 0; r < 3; ++r) {
-            for (int c = 0; c < 3; ++c) R[3 * r + c] = (float)st->P[4 * r + c];
-            tp[r] = (float)st->P[4 * r + 3];
-        }
+        const double* P = a.st->P;
         if (SRC == SRC_EVAL) {
-            for (int q = 0; q < 9; ++q) Rw[q] = R[q];
-            for (int r = 0; r < 3; ++r) tw[r] = tp[r];
+            for (int r = 0; r < 3; ++r) {
+                for (int c = 0; c < 3; ++c) R[3 * r + c] = P[4 * r + c];
+                tw[r] = P[4 * r + 3];
+            }
         } else {
             const float* u = a.templ + 6 * (size_t)k;
-            const float wr = (float)(st->s[0] * kPi / 180.0), wt = (float)(st->s[1] / 100.0);
-            float dR[9];
-            so3_exp_f(wr * u[0], wr * u[1], wr * u[2], dR);
-            const float dt[3] = {wt * u[3], wt * u[4], wt * u[5]};
+            const double wr = a.st->s[0] * kPi / 180.0, wt = a.st->s[1] / 100.0;
+            const double dw[3] = {wr * (double)u[0], wr * (double)u[1], wr * (double)u[2]};
+            double dR[9];
+            so3_exp_d(dw, dR);
             for (int r = 0; r < 3; ++r) {
                 for (int c = 0; c < 3; ++c)
-                    Rw[3 * r + c] = dR[3 * r] * R[c] + dR[3 * r + 1] * R[3 + c] + dR[3 * r + 2] * R[6 + c];
-                const float tr = a.compose_mode == 0 ? dR[3 * r] * tp[0] + dR[3 * r + 1] * tp[1] + dR[3 * r + 2] * tp[2]
-                                                     : tp[r];
-                tw[r] = tr + dt[r];
+                    R[3 * r + c] = dR[3 * r] * P[c] + dR[3 * r + 1] * P[4 + c] + dR[3 * r + 2] * P[8 + c];
+                const double tr = a.compose_mode == 0 ? dR[3 * r] * P[3] + dR[3 * r + 1] * P[7] + dR[3 * r + 2] * P[11]
+                                                      : P[4 * r + 3];
+                tw[r] = tr + wt * (double)u[3 + r];
             }
         }
     }
-    to_grid(Rw, tw, 1.0 / a.vs, a.org, sT[t]);
+    make_particle(R, tw, a, sP[t]);
 }
 
 // Block-wide argmin of (E, k) with the lowest k among equal E.
@@ -420,13 +473,16 @@ __device__ inline void argmin_pair(float& e, int& k, float* se, int* sk)
 }
 
 template <int SRC, int VARIANT>
-__global__ void __launch_bounds__(FIT_THREADS) fitness_kernel(FitArgs a)
+__global__ void __launch_bounds__(FIT_THREADS, 3) fitness_kernel(FitArgs a)
 {
-    __shared__ float sT[KC][12];
+    __shared__ Particle sP[KC];
     __shared__ float accS[FIT_WARPS][KC];
     __shared__ int accC[FIT_WARPS][KC];
     __shared__ int s_last;
     __shared__ int s_skip;
+    __shared__ int s_mode;
+    __shared__ float s_spread[2];
+    __shared__ float s_red[FIT_WARPS];
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int k_begin = blockIdx.x * KC;
@@ -446,7 +502,31 @@ __global__ void __launch_bounds__(FIT_THREADS) fitness_kernel(FitArgs a)
     }
     __syncthreads();
     const bool skip = s_skip != 0;
-    if (!skip) build_transforms<SRC>(a, k_begin, kc, sT);
+    if (!skip) build_particles<SRC>(a, k_begin, kc, sP);
+    __syncthreads();
+    // spread of the chunk's particles: translation (voxels) and rotation
+    // (voxels per metre) relative to its first particle
+    if (tid == 0) {
+        float dt = 0.0f, dr = 0.0f;
+        if (!skip) {
+            const Particle& P0 = sP[0];
+            const float o0[3] = {(float)(kMagicBits - __float_as_int(P0.u.w)), (float)(kMagicBits - __float_as_int(P0.m.x)),
+                                 (float)(kMagicBits - __float_as_int(P0.m.y))};
+            for (int k = 1; k < kc; ++k) {
+                const Particle& P = sP[k];
+                const float ok_[3] = {(float)(kMagicBits - __float_as_int(P.u.w)), (float)(kMagicBits - __float_as_int(P.m.x)),
+                                      (float)(kMagicBits - __float_as_int(P.m.y))};
+                dt = fmaxf(dt, fabsf((ok_[0] + P.h0.w) - (o0[0] + P0.h0.w)));
+                dt = fmaxf(dt, fabsf((ok_[1] + P.h1.w) - (o0[1] + P0.h1.w)));
+                dt = fmaxf(dt, fabsf((ok_[2] + P.h2.w) - (o0[2] + P0.h2.w)));
+                dr = fmaxf(dr, fabsf(P.h0.x - P0.h0.x) + fabsf(P.h0.y - P0.h0.y) + fabsf(P.h0.z - P0.h0.z));
+                dr = fmaxf(dr, fabsf(P.h1.x - P0.h1.x) + fabsf(P.h1.y - P0.h1.y) + fabsf(P.h1.z - P0.h1.z));
+                dr = fmaxf(dr, fabsf(P.h2.x - P0.h2.x) + fabsf(P.h2.y - P0.h2.y) + fabsf(P.h2.z - P0.h2.z));
+            }
+        }
+        s_spread[0] = dt;
+        s_spread[1] = dr;
+    }
     __syncthreads();
 
     const int N = a.n_dev ? *a.n_dev : a.n_host;
@@ -454,11 +534,11 @@ __global__ void __launch_bounds__(FIT_THREADS) fitness_kernel(FitArgs a)
     const long long beg = Ne * blockIdx.y / a.n_ptiles;
     const long long end = Ne * (blockIdx.y + 1) / a.n_ptiles;
     const int nx = a.nx, nxy = a.nx * a.ny;
-    const float gmx = (float)(a.nx - 1), gmy = (float)(a.ny - 1), gmz = (float)(a.nz - 1);
 
     if (!skip) {
         for (long long sub = beg; sub < end; sub += SUBTILE) {
             float px[PPT], py[PPT], pz[PPT];
+            float r2 = 0.0f;
 #pragma unroll
             for (int p = 0; p < PPT; ++p) {
                 const long long e = sub + p * FIT_THREADS + tid;
@@ -467,36 +547,61 @@ __global__ void __launch_bounds__(FIT_THREADS) fitness_kernel(FitArgs a)
                     px[p] = q.x;
                     py[p] = q.y;
                     pz[p] = q.z;
+                    r2 = fmaxf(r2, q.x * q.x + q.y * q.y + q.z * q.z);
                 } else {
                     px[p] = NAN;
                     py[p] = NAN;
                     pz[p] = NAN;
                 }
             }
-            for (int kk = 0; kk < kc; ++kk) {
-                const float4 r0 = *reinterpret_cast<const float4*>(&sT[kk][0]);
-                const float4 r1 = *reinterpret_cast<const float4*>(&sT[kk][4]);
-                const float4 r2 = *reinterpret_cast<const float4*>(&sT[kk][8]);
+            // mapping of this sub-tile: when every particle puts a point in
+            // (nearly) the same cell, lanes take particles and share a point,
+            // so each gather of a warp touches one or two sectors; otherwise
+            // lanes take neighbouring image points of one particle
+            for (int o = 16; o > 0; o >>= 1) r2 = fmaxf(r2, __shfl_xor_sync(0xffffffffu, r2, o));
+            if (lane == 0) s_red[warp] = r2;
+            __syncthreads();
+            if (tid == 0) {
+                float m = 0.0f;
+                for (int w = 0; w < FIT_WARPS; ++w) m = fmaxf(m, s_red[w]);
+                s_mode = (s_spread[0] + s_spread[1] * sqrtf(m)) < a.pm_threshold;
+            }
+            __syncthreads();
+            if (!s_mode) {
+                for (int kk = 0; kk < kc; ++kk) {
+                    Xform X;
+                    load_xform(sP[kk], X);
+                    float s = 0.0f;
+                    int c = 0;
+#pragma unroll
+                    for (int p = 0; p < PPT; ++p) sample<VARIANT>(a, nx, nxy, X, px[p], py[p], pz[p], s, c);
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) {
+                        s += __shfl_xor_sync(0xffffffffu, s, o);
+                        c += __shfl_xor_sync(0xffffffffu, c, o);
+                    }
+                    if (lane == 0) {
+                        accS[warp][kk] += s;
+                        accC[warp][kk] += c;
+                    }
+                }
+            } else {
+                Xform X;
+                load_xform(sP[lane < kc ? lane : 0], X);
                 float s = 0.0f;
                 int c = 0;
 #pragma unroll
                 for (int p = 0; p < PPT; ++p) {
-                    const float gx = fmaf(r0.x, px[p], fmaf(r0.y, py[p], fmaf(r0.z, pz[p], r0.w)));
-                    const float gy = fmaf(r1.x, px[p], fmaf(r1.y, py[p], fmaf(r1.z, pz[p], r1.w)));
-                    const float gz = fmaf(r2.x, px[p], fmaf(r2.y, py[p], fmaf(r2.z, pz[p], r2.w)));
-                    if (VARIANT == 0)
-                        sample_encoded(a.tsdf, nx, nxy, gmx, gmy, gmz, gx, gy, gz, s, c);
-                    else
-                        sample_plain(a.tsdf, a.weight, nx, nxy, gmx, gmy, gmz, gx, gy, gz, s, c);
+                    for (int j = 0; j < 32; ++j) {
+                        const float x = __shfl_sync(0xffffffffu, px[p], j);
+                        const float y = __shfl_sync(0xffffffffu, py[p], j);
+                        const float z = __shfl_sync(0xffffffffu, pz[p], j);
+                        sample<VARIANT>(a, nx, nxy, X, x, y, z, s, c);
+                    }
                 }
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) {
-                    s += __shfl_xor_sync(0xffffffffu, s, o);
-                    c += __shfl_xor_sync(0xffffffffu, c, o);
-                }
-                if (lane == 0) {
-                    accS[warp][kk] += s;
-                    accC[warp][kk] += c;
+                if (lane < kc) {
+                    accS[warp][lane] += s;
+                    accC[warp][lane] += c;
                 }
             }
         }
@@ -734,11 +839,17 @@ int choose_ptiles(int dev, int chunks, long long ne_max)
     return (int)std::max(1LL, tiles);
 }
 
+// variant bit 0: 1 = plain layout (reads the weights); bits 1-2: lane
+// mapping, 0 = chosen per sub-tile, 1 = points on lanes, 2 = particles on lanes.
+constexpr float kParticleLanesBelow = 1.5f;  // voxels of particle spread
+
 template <int SRC>
-void launch_fitness(const FitArgs& a, int variant, int chunks, cudaStream_t s)
+void launch_fitness(FitArgs a, int variant, int chunks, cudaStream_t s)
 {
+    const int mapping = (variant >> 1) & 3;
+    a.pm_threshold = mapping == 1 ? -1.0f : mapping == 2 ? INFINITY : kParticleLanesBelow;
     dim3 grid(chunks, a.n_ptiles);
-    if (variant == 0)
+    if ((variant & 1) == 0)
         fitness_kernel<SRC, 0><<<grid, FIT_THREADS, 0, s>>>(a);
     else
         fitness_kernel<SRC, 1><<<grid, FIT_THREADS, 0, s>>>(a);

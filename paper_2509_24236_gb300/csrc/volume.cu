@@ -43,7 +43,7 @@ struct IntegArgs {
     float radius;                       // bounding radius of a tile (+ margin)
 };
 
-__global__ void __launch_bounds__(TX * TY) integrate_kernel(IntegArgs a)
+__global__ void __launch_bounds__(TX * TY, 4) integrate_kernel(IntegArgs a)
 {
     __shared__ float s_base[4];
     __shared__ float s_step[9];
@@ -223,7 +223,7 @@ pf_status pf_reset_volume(pf_volume* v, void* stream)
 
 pf_status pf_set_fitness_variant(pf_volume* v, int variant)
 {
-    if (!v || variant < 0 || variant > 1) return PF_ERR_INVALID_ARG;
+    if (!v || variant < 0 || variant > 5) return PF_ERR_INVALID_ARG;
     v->fitness_variant = variant;
     return PF_OK;
 }
