@@ -69,7 +69,10 @@ typedef enum { PF_F32 = 0, PF_F16 = 1, PF_BF16 = 2, PF_FP8E4M3 = 3 } pf_dtype;
 /* Dense TSDF grid (Sec. III: "a tensor that records the distance value in
  * each 3D grid").  nx, ny, nz in [2, 4096] with nx*ny*nz < 2^31;
  * voxel_size > 0; trunc (tau, metres) > 0; max_weight in [1, 65535] caps the
- * running-average weight; weight_u8 must be 0 in this version. */
+ * running-average weight; weight_u8 must be 0 in this version.
+ * cell_view: the fitness reads a second copy of the grid in which the eight
+ * corner values of every cell are contiguous (32 bytes per node, kept up to
+ * date by fusion); 0 = when it needs at most 16 GiB, 1 = always, -1 = never. */
 typedef struct {
     int nx, ny, nz;
     float voxel_size;
@@ -78,6 +81,7 @@ typedef struct {
     pf_dtype tsdf_dtype;
     int weight_u8;
     int max_weight;
+    int cell_view;
 } pf_volume_desc;
 
 /* Parameters of the randomized optimization (Sec. III-B, defaults Sec. IV-A:
@@ -228,16 +232,19 @@ PF_API pf_status pf_raycast(const pf_volume* vol, const pf_intrinsics* intr, con
                      float* depth_out_dev, float* normal_out_dev_or_null, void* cuda_stream);
 
 /* Fitness kernel variant used by pf_fitness and the search of this volume,
- * variant = layout + 2 * mapping.
- *   layout  0 (default): reads only the tsdf array, whose encoding makes a
- *           cell's validity a property of its interpolated value;
- *           1: the plain form that also reads the weights and tests all
- *           eight nodes explicitly (the performance baseline).
- *   mapping 0 (default): chosen per block of points from the spread of the
- *           particles; 1: neighbouring points on the lanes of a warp;
+ * variant = layout + 4 * mapping (0 is the default everywhere).
+ *   layout  0: the cell view when the volume has one, else 2;
+ *           1: the plain form: tsdf and weight arrays, all eight nodes
+ *              tested explicitly (the performance baseline);
+ *           2: the tsdf array alone, whose encoding makes a cell's validity
+ *              a property of its interpolated value;
+ *           3: the cell view (PF_ERR_INVALID_ARG if the volume has none).
+ *   mapping 0: chosen per block of points from the spread of the particles;
+ *           1: neighbouring points on the lanes of a warp;
  *           2: particles on the lanes of a warp.
  * All variants evaluate the same samples: counts are identical and fitness
- * values differ only by the float summation order. */
+ * values differ only by the float summation order (layouts are bit-identical
+ * for a given mapping). */
 PF_API pf_status pf_set_fitness_variant(pf_volume* vol, int variant);
 
 PF_API const char* pf_status_string(pf_status status);
@@ -249,7 +256,8 @@ PF_API unsigned long long pf_launch_count(void);
 
 /* When enabled, every launch of the named kernel class ("fitness": the
  * search and pf_fitness launches; "fitness1": the single-pose evaluation of
- * the mean update; "integrate", "backproject", "raycast") is bracketed by
+ * the mean update; "integrate"; "refresh": the cell-view update after
+ * fusion; "backproject"; "raycast") is bracketed by
  * CUDA events on its stream.  pf_kernel_timing synchronises those events, returns the summed
  * device time (ms) and launch count since the last query, and clears them. */
 PF_API pf_status pf_set_kernel_timing(int enable);

@@ -30,7 +30,7 @@ class pf_intrinsics(C.Structure):
 class pf_volume_desc(C.Structure):
     _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int), ("voxel_size", C.c_float),
                 ("trunc", C.c_float), ("origin", C.c_float * 3), ("tsdf_dtype", C.c_int),
-                ("weight_u8", C.c_int), ("max_weight", C.c_int)]
+                ("weight_u8", C.c_int), ("max_weight", C.c_int), ("cell_view", C.c_int)]
 
 
 class pf_track_params(C.Structure):
@@ -309,14 +309,16 @@ def track_params(templates_dev, n_iters=20, k_sched=(1024, 3072, 10240), decim_s
 class Volume:
     """A TSDF volume on the current CUDA device (owns pf_volume)."""
 
-    def __init__(self, nx, ny, nz, voxel_size, trunc, origin=(0.0, 0.0, 0.0), max_weight=255, stream=None):
-        self.desc = pf_volume_desc(nx, ny, nz, voxel_size, trunc, (C.c_float * 3)(*origin), PF_F32, 0, max_weight)
+    def __init__(self, nx, ny, nz, voxel_size, trunc, origin=(0.0, 0.0, 0.0), max_weight=255, cell_view=0,
+                 stream=None):
+        self.desc = pf_volume_desc(nx, ny, nz, voxel_size, trunc, (C.c_float * 3)(*origin), PF_F32, 0, max_weight,
+                                   cell_view)
         self.n_nodes = nx * ny * nz
         self.handle = pf_create_volume(self.desc, stream)
 
     @classmethod
-    def from_grid(cls, grid, max_weight=255):
-        return cls(grid.nx, grid.ny, grid.nz, grid.voxel_size, grid.trunc, grid.origin, max_weight)
+    def from_grid(cls, grid, max_weight=255, cell_view=0):
+        return cls(grid.nx, grid.ny, grid.nz, grid.voxel_size, grid.trunc, grid.origin, max_weight, cell_view)
 
     def close(self):
         if getattr(self, "handle", None):

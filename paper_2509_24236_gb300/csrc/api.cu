@@ -31,7 +31,7 @@ TimingState& timing()
     return t;
 }
 
-const char* kClassNames[KC_COUNT] = {"fitness", "fitness1", "integrate", "backproject", "raycast"};
+const char* kClassNames[KC_COUNT] = {"fitness", "fitness1", "integrate", "refresh", "backproject", "raycast"};
 
 }  // namespace
 

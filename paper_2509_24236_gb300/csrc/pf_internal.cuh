@@ -64,12 +64,20 @@ struct pf_workspace {
     pf_track_stats* stats = nullptr; // 1
 };
 
+// Fusion works on tiles of 32 x 8 x 8 nodes; the cell view is refreshed
+// tile by tile after fusion.
+constexpr int PF_TX = 32, PF_TY = 8, PF_TZ = 8;
+
 struct pf_volume {
     pf_volume_desc desc;
     int device = 0;
     size_t n_nodes = 0;
-    float* tsdf = nullptr;    // encoded, see above
+    float* tsdf = nullptr;     // encoded, see above
     float* weight = nullptr;
+    float4* cells = nullptr;   // cell view: 2 float4 per node (the cell whose lower corner it is)
+    int* tile_stamp = nullptr; // per fusion tile: stamp of the last fusion that reached it
+    int stamp = 0;             // fusions so far
+    int tiles[3] = {0, 0, 0};
     int fitness_variant = 0;
     pf_workspace ws;
 };
@@ -83,7 +91,7 @@ extern std::atomic<unsigned long long> g_launches;
 
 inline void count_launch(unsigned n = 1) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 
-enum KernelClass { KC_FITNESS = 0, KC_FITNESS1, KC_INTEGRATE, KC_BACKPROJECT, KC_RAYCAST, KC_COUNT };
+enum KernelClass { KC_FITNESS = 0, KC_FITNESS1, KC_INTEGRATE, KC_REFRESH, KC_BACKPROJECT, KC_RAYCAST, KC_COUNT };
 
 // Event bracketing of launches (no-ops unless timing is enabled).
 void timing_begin(KernelClass kc, cudaStream_t s);

@@ -179,6 +179,7 @@ struct FitArgs {
     // volume
     const float* tsdf;
     const float* weight;
+    const float4* cells;
     int nx, ny, nz;
     double vs;
     double org[3];
@@ -390,6 +391,34 @@ __device__ __forceinline__ void sample_plain(const float* __restrict__ tsdf, con
     }
 }
 
+// Cell-view sample: the eight corners of the cell are one 32-byte sector,
+// fetched as two 16-byte loads; same arithmetic as sample_encoded.
+__device__ __forceinline__ void sample_cells(const float4* __restrict__ cells, int nx, int nxy, const Xform& X,
+                                             float gx, float gy, float gz, float& s, int& c)
+{
+    if (gx >= X.lo[0] && gx < X.hi[0] && gy >= X.lo[1] && gy < X.hi[1] && gz >= X.lo[2] && gz < X.hi[2]) {
+        const float M = 12582912.0f;
+        const float rx = __fadd_rd(gx, M), ry = __fadd_rd(gy, M), rz = __fadd_rd(gz, M);
+        const int idx = (__float_as_int(rx) - X.mg[0]) + nx * (__float_as_int(ry) - X.mg[1]) +
+                        nxy * (__float_as_int(rz) - X.mg[2]);
+        const float fx = gx - (rx - M), fy = gy - (ry - M), fz = gz - (rz - M);
+        const float4* p = cells + 2 * (size_t)idx;
+        const float4 lo = __ldg(p), hi = __ldg(p + 1);
+        const float x00 = fmaf(fx, lo.y - lo.x, lo.x);
+        const float x10 = fmaf(fx, lo.w - lo.z, lo.z);
+        const float x01 = fmaf(fx, hi.y - hi.x, hi.x);
+        const float x11 = fmaf(fx, hi.w - hi.z, hi.z);
+        const float y0 = fmaf(fy, x10 - x00, x00);
+        const float y1 = fmaf(fy, x11 - x01, x01);
+        const float t = fabsf(fmaf(fz, y1 - y0, y0));
+        if (t < INFINITY) {
+            s += t;
+            c += 1;
+        }
+    }
+}
+
+// VARIANT: 0 encoded tsdf nodes, 1 plain (tsdf + weight), 2 cell view.
 template <int VARIANT>
 __device__ __forceinline__ void sample(const FitArgs& a, int nx, int nxy, const Xform& X, float x, float y, float z,
                                        float& s, int& c)
@@ -398,8 +427,10 @@ __device__ __forceinline__ void sample(const FitArgs& a, int nx, int nxy, const 
     apply(X, x, y, z, gx, gy, gz);
     if (VARIANT == 0)
         sample_encoded(a.tsdf, nx, nxy, X, gx, gy, gz, s, c);
-    else
+    else if (VARIANT == 1)
         sample_plain(a.tsdf, a.weight, nx, nxy, X, gx, gy, gz, s, c);
+    else
+        sample_cells(a.cells, nx, nxy, X, gx, gy, gz, s, c);
 }
 
 // Particles k_begin .. k_begin+kc-1 of this launch into shared memory, in FP64
@@ -839,20 +870,28 @@ int choose_ptiles(int dev, int chunks, long long ne_max)
     return (int)std::max(1LL, tiles);
 }
 
-// variant bit 0: 1 = plain layout (reads the weights); bits 1-2: lane
-// mapping, 0 = chosen per sub-tile, 1 = points on lanes, 2 = particles on lanes.
-constexpr float kParticleLanesBelow = 1.5f;  // voxels of particle spread
+// variant = layout + 4 * mapping (see pf_set_fitness_variant).  Measured on
+// the 640x480 / 512^3 workload, particles on lanes win below a spread of
+// about 0.5 degree and 0.5 cm with the cell view (~5 voxels by the bound
+// used here) and below about 1 degree and 1 cm on the node array (~12).
+constexpr float kParticleLanesBelowCells = 5.0f;
+constexpr float kParticleLanesBelowNodes = 12.0f;
 
 template <int SRC>
-void launch_fitness(FitArgs a, int variant, int chunks, cudaStream_t s)
+void launch_fitness(FitArgs a, int variant, bool has_cells, int chunks, cudaStream_t s)
 {
-    const int mapping = (variant >> 1) & 3;
-    a.pm_threshold = mapping == 1 ? -1.0f : mapping == 2 ? INFINITY : kParticleLanesBelow;
+    const int mapping = (variant >> 2) & 3;
+    int layout = variant & 3;
+    if (layout == 0) layout = has_cells ? 3 : 2;
+    const float auto_threshold = layout == 3 ? kParticleLanesBelowCells : kParticleLanesBelowNodes;
+    a.pm_threshold = mapping == 1 ? -1.0f : mapping == 2 ? INFINITY : auto_threshold;
     dim3 grid(chunks, a.n_ptiles);
-    if ((variant & 1) == 0)
+    if (layout == 2)
         fitness_kernel<SRC, 0><<<grid, FIT_THREADS, 0, s>>>(a);
-    else
+    else if (layout == 1)
         fitness_kernel<SRC, 1><<<grid, FIT_THREADS, 0, s>>>(a);
+    else
+        fitness_kernel<SRC, 2><<<grid, FIT_THREADS, 0, s>>>(a);
     pf::count_launch();
 }
 
@@ -860,6 +899,7 @@ void fill_volume_args(FitArgs& a, const pf_volume* v)
 {
     a.tsdf = v->tsdf;
     a.weight = v->weight;
+    a.cells = v->cells;
     a.nx = v->desc.nx;
     a.ny = v->desc.ny;
     a.nz = v->desc.nz;
@@ -997,7 +1037,7 @@ pf_status pf_fitness(const pf_volume* cv, const float* points_dev, int n, const 
     a.out_C = count_dev;
     cudaStream_t s = (cudaStream_t)stream;
     pf::timing_begin(pf::KC_FITNESS, s);
-    launch_fitness<SRC_POSES>(a, v->fitness_variant, chunks, s);
+    launch_fitness<SRC_POSES>(a, v->fitness_variant, v->cells != nullptr, chunks, s);
     pf::timing_end(pf::KC_FITNESS, s);
     PF_LAUNCHED();
     return PF_OK;
@@ -1058,14 +1098,14 @@ pf_status pf_track_frame_async(pf_volume* v, const float* depth_dev, const pf_in
         a.n_ptiles = choose_ptiles(v->device, chunks, ne_max);
         if ((size_t)a.n_ptiles * K > (size_t)w.part_cap) return PF_ERR_INVALID_ARG;
         pf::timing_begin(pf::KC_FITNESS, s);
-        launch_fitness<SRC_SEARCH>(a, v->fitness_variant, chunks, s);
+        launch_fitness<SRC_SEARCH>(a, v->fitness_variant, v->cells != nullptr, chunks, s);
         pf::timing_end(pf::KC_FITNESS, s);
         if (p->update_mode == 0) {
             FitArgs e = a;
             e.K = 1;
             e.n_ptiles = choose_ptiles(v->device, 1, ne_max);
             pf::timing_begin(pf::KC_FITNESS1, s);
-            launch_fitness<SRC_EVAL>(e, v->fitness_variant, 1, s);
+            launch_fitness<SRC_EVAL>(e, v->fitness_variant, v->cells != nullptr, 1, s);
             pf::timing_end(pf::KC_FITNESS1, s);
         }
     }

@@ -24,7 +24,7 @@
 
 namespace {
 
-constexpr int TX = 32, TY = 8, TZ = 8;
+constexpr int TX = PF_TX, TY = PF_TY, TZ = PF_TZ;
 
 struct IntegArgs {
     float* tsdf;
@@ -41,6 +41,8 @@ struct IntegArgs {
     float plane[4][3];                  // inward normals of the four side planes of the frustum
     float zfar;                         // nodes deeper than this are never updated
     float radius;                       // bounding radius of a tile (+ margin)
+    int* tile_stamp;                    // tiles not culled get `stamp` (null: no cell view)
+    int stamp;
 };
 
 __global__ void __launch_bounds__(TX * TY, 4) integrate_kernel(IntegArgs a)
@@ -78,6 +80,8 @@ __global__ void __launch_bounds__(TX * TY, 4) integrate_kernel(IntegArgs a)
             if (d < -a.radius) skip = 1;
         }
         s_skip = skip;
+        if (!skip && a.tile_stamp)
+            a.tile_stamp[blockIdx.x + gridDim.x * (blockIdx.y + (size_t)gridDim.y * blockIdx.z)] = a.stamp;
     }
     __syncthreads();
     if (s_skip) return;
@@ -131,6 +135,68 @@ __global__ void fill_kernel(float* tsdf, float* weight, size_t n)
     }
 }
 
+// Cell view: for every cell (lower corner node i, j, k) its eight encoded
+// corner values, x fastest: float4 (v000 v100 v010 v110), float4 (v001 v101
+// v011 v111).  A cell depends on the nodes of its own fusion tile and of the
+// next tiles along +x, +y, +z, so a tile is rewritten when any of those was
+// reached by the last fusion (or always, after a reset or upload).
+struct RefreshArgs {
+    const float* tsdf;
+    float4* cells;
+    int nx, ny, nz;
+    const int* tile_stamp;
+    int stamp;
+    int all;
+};
+
+__global__ void __launch_bounds__(TX * TY, 4) cells_refresh_kernel(RefreshArgs a)
+{
+    __shared__ int s_need;
+    if (threadIdx.x == 0 && threadIdx.y == 0) {
+        int need = a.all;
+        for (int q = 0; q < 8 && !need; ++q) {
+            const unsigned bx = blockIdx.x + (q & 1), by = blockIdx.y + ((q >> 1) & 1), bz = blockIdx.z + (q >> 2);
+            if (bx < gridDim.x && by < gridDim.y && bz < gridDim.z)
+                need = a.tile_stamp[bx + gridDim.x * (by + (size_t)gridDim.y * bz)] == a.stamp;
+        }
+        s_need = need;
+    }
+    __syncthreads();
+    if (!s_need) return;
+    const int i = blockIdx.x * TX + threadIdx.x, j = blockIdx.y * TY + threadIdx.y;
+    if (i >= a.nx - 1 || j >= a.ny - 1) return;
+    const size_t nx = a.nx, nxy = (size_t)a.nx * a.ny;
+    for (int dz = 0; dz < TZ; ++dz) {
+        const int k = blockIdx.z * TZ + dz;
+        if (k >= a.nz - 1) break;
+        const size_t idx = i + nx * j + nxy * k;
+        const float* p = a.tsdf + idx;
+        const float4 lo = make_float4(p[0], p[1], p[nx], p[nx + 1]);
+        const float4 hi = make_float4(p[nxy], p[nxy + 1], p[nxy + nx], p[nxy + nx + 1]);
+        a.cells[2 * idx] = lo;
+        a.cells[2 * idx + 1] = hi;
+    }
+}
+
+pf_status enqueue_refresh(pf_volume* v, cudaStream_t s, int all)
+{
+    if (!v->cells) return PF_OK;
+    RefreshArgs r;
+    r.tsdf = v->tsdf;
+    r.cells = v->cells;
+    r.nx = v->desc.nx;
+    r.ny = v->desc.ny;
+    r.nz = v->desc.nz;
+    r.tile_stamp = v->tile_stamp;
+    r.stamp = v->stamp;
+    r.all = all;
+    dim3 grid(v->tiles[0], v->tiles[1], v->tiles[2]);
+    cells_refresh_kernel<<<grid, dim3(TX, TY), 0, s>>>(r);
+    pf::count_launch();
+    PF_LAUNCHED();
+    return PF_OK;
+}
+
 pf_status check_desc(const pf_volume_desc* d)
 {
     if (!d) return PF_ERR_INVALID_ARG;
@@ -142,6 +208,7 @@ pf_status check_desc(const pf_volume_desc* d)
     for (int a = 0; a < 3; ++a)
         if (!std::isfinite(d->origin[a])) return PF_ERR_INVALID_ARG;
     if (d->max_weight < 1 || d->max_weight > 65535) return PF_ERR_INVALID_ARG;
+    if (d->cell_view < -1 || d->cell_view > 1) return PF_ERR_INVALID_ARG;
     if (d->tsdf_dtype != PF_F32 || d->weight_u8 != 0) return PF_ERR_UNSUPPORTED;
     return PF_OK;
 }
@@ -152,7 +219,7 @@ pf_status enqueue_reset(pf_volume* v, cudaStream_t s)
     fill_kernel<<<blocks, 256, 0, s>>>(v->tsdf, v->weight, v->n_nodes);
     pf::count_launch();
     PF_LAUNCHED();
-    return PF_OK;
+    return enqueue_refresh(v, s, 1);
 }
 
 bool finite_pose(const double* P)
@@ -175,12 +242,24 @@ pf_status pf_create_volume(const pf_volume_desc* desc, void* stream, pf_volume**
     pf_volume* v = new pf_volume();
     v->desc = *desc;
     v->n_nodes = (size_t)desc->nx * desc->ny * desc->nz;
+    v->tiles[0] = (desc->nx + TX - 1) / TX;
+    v->tiles[1] = (desc->ny + TY - 1) / TY;
+    v->tiles[2] = (desc->nz + TZ - 1) / TZ;
+    const size_t view_bytes = v->n_nodes * 2 * sizeof(float4);
+    const bool view = desc->cell_view == 1 || (desc->cell_view == 0 && view_bytes <= (16ull << 30));
     cudaError_t e = cudaGetDevice(&v->device);
     if (e == cudaSuccess) e = cudaMalloc(&v->tsdf, v->n_nodes * sizeof(float));
     if (e == cudaSuccess) e = cudaMalloc(&v->weight, v->n_nodes * sizeof(float));
+    if (e == cudaSuccess && view) e = cudaMalloc(&v->cells, view_bytes);
+    if (e == cudaSuccess && view)
+        e = cudaMalloc(&v->tile_stamp, sizeof(int) * (size_t)v->tiles[0] * v->tiles[1] * v->tiles[2]);
+    if (e == cudaSuccess && view)
+        e = cudaMemset(v->tile_stamp, 0, sizeof(int) * (size_t)v->tiles[0] * v->tiles[1] * v->tiles[2]);
     if (e != cudaSuccess) {
         cudaFree(v->tsdf);
         cudaFree(v->weight);
+        cudaFree(v->cells);
+        cudaFree(v->tile_stamp);
         delete v;
         cudaGetLastError();
         return pf::cuda_status(e);
@@ -200,6 +279,8 @@ pf_status pf_destroy_volume(pf_volume* v)
     cudaDeviceSynchronize();
     cudaFree(v->tsdf);
     cudaFree(v->weight);
+    cudaFree(v->cells);
+    cudaFree(v->tile_stamp);
     pf_workspace& w = v->ws;
     cudaFree(w.points);
     cudaFree(w.block_counts);
@@ -223,7 +304,7 @@ pf_status pf_reset_volume(pf_volume* v, void* stream)
 
 pf_status pf_set_fitness_variant(pf_volume* v, int variant)
 {
-    if (!v || variant < 0 || variant > 5) return PF_ERR_INVALID_ARG;
+    if (!v || variant < 0 || variant > 11 || (variant & 3) == 3 && !v->cells) return PF_ERR_INVALID_ARG;
     v->fitness_variant = variant;
     return PF_OK;
 }
@@ -241,6 +322,9 @@ pf_status pf_volume_upload(pf_volume* v, const float* tsdf_host, const float* we
     PF_CUDA(cudaDeviceSynchronize());
     PF_CUDA(cudaMemcpy(v->tsdf, enc.data(), v->n_nodes * sizeof(float), cudaMemcpyHostToDevice));
     PF_CUDA(cudaMemcpy(v->weight, weight_host, v->n_nodes * sizeof(float), cudaMemcpyHostToDevice));
+    pf_status st = enqueue_refresh(v, 0, 1);
+    if (st != PF_OK) return st;
+    PF_CUDA(cudaDeviceSynchronize());
     return PF_OK;
 }
 
@@ -292,13 +376,18 @@ pf_status integrate_impl(pf_volume* v, const float* depth_dev, const pf_intrinsi
     const double vs = d.voxel_size;
     a.radius = (float)(0.5 * vs * sqrt((double)((TX - 1) * (TX - 1) + (TY - 1) * (TY - 1) + (TZ - 1) * (TZ - 1)))
                        + 0.01 * vs + 1e-3);
-    dim3 grid((d.nx + TX - 1) / TX, (d.ny + TY - 1) / TY, (d.nz + TZ - 1) / TZ);
+    a.tile_stamp = v->tile_stamp;
+    a.stamp = ++v->stamp;
+    dim3 grid(v->tiles[0], v->tiles[1], v->tiles[2]);
     pf::timing_begin(pf::KC_INTEGRATE, s);
     integrate_kernel<<<grid, dim3(TX, TY), 0, s>>>(a);
     pf::count_launch();
     pf::timing_end(pf::KC_INTEGRATE, s);
     PF_LAUNCHED();
-    return PF_OK;
+    pf::timing_begin(pf::KC_REFRESH, s);
+    st = enqueue_refresh(v, s, 0);
+    pf::timing_end(pf::KC_REFRESH, s);
+    return st;
 }
 
 __global__ void compose_kernel(const double* A, const double* B, double* out)

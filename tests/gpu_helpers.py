@@ -74,6 +74,7 @@ def compare_fitness(E_gpu, C_gpu, orc, rel=1e-5, floor=1e-7):
     absolute `floor` (the FP32 position-quantisation floor of near-perfect
     alignments).  Returns the number of poses that had ambiguous points."""
     from itertools import combinations
+    from math import comb
     K = len(orc.E)
     assert E_gpu.shape == (K,) and C_gpu.shape == (K,)
     for k in range(K):
@@ -84,8 +85,15 @@ def compare_fitness(E_gpu, C_gpu, orc, rel=1e-5, floor=1e-7):
             assert np.isinf(E_gpu[k])
             continue
         assert a <= orc.vals.shape[1] if orc.vals is not None else a == 0
-        vals = orc.vals[k, :a] if a else np.zeros(0)
-        best = min(abs(E_gpu[k] - (orc.S[k] + sum(sub)) / C_gpu[k]) for sub in combinations(vals, m))
-        ref = (orc.S[k] + (np.sort(vals)[:m].sum() if m else 0.0)) / C_gpu[k]
+        vals = np.sort(orc.vals[k, :a]) if a else np.zeros(0)
+        ref = (orc.S[k] + vals[:m].sum()) / C_gpu[k]
+        if comb(a, m) <= 5000:
+            best = min(abs(E_gpu[k] - (orc.S[k] + sum(sub)) / C_gpu[k]) for sub in combinations(vals, m))
+        else:
+            # too many subsets to try: the sum must lie between the m smallest
+            # and the m largest values
+            lo = (orc.S[k] + vals[:m].sum()) / C_gpu[k]
+            hi = (orc.S[k] + vals[a - m:].sum()) / C_gpu[k]
+            best = max(0.0, lo - E_gpu[k], E_gpu[k] - hi)
         assert best <= rel * ref + floor, (k, E_gpu[k], ref, best / ref)
     return int(np.count_nonzero(orc.amb)) if orc.amb is not None else 0
