@@ -595,7 +595,8 @@ __global__ void __launch_bounds__(FIT_THREADS, 3) fitness_kernel(FitArgs a)
             if (tid == 0) {
                 float m = 0.0f;
                 for (int w = 0; w < FIT_WARPS; ++w) m = fmaxf(m, s_red[w]);
-                s_mode = (s_spread[0] + s_spread[1] * sqrtf(m)) < a.pm_threshold;
+                // (a chunk of fewer than 24 particles would leave lanes idle)
+                s_mode = kc >= 24 && (s_spread[0] + s_spread[1] * sqrtf(m)) < a.pm_threshold;
             }
             __syncthreads();
             if (!s_mode) {

@@ -187,8 +187,11 @@ def test_fitness_parity(pf, K, N, spread):
             E, C = vol.fitness(to_dev(pts), to_dev(poses))
             results[layout, mapping] = (E.cpu().numpy(), C.cpu().numpy())
             compare_fitness(*results[layout, mapping], orc)
-        for layout in (2, 3):
-            assert np.array_equal(results[layout, mapping][0], results[1, mapping][0])
+        # the same mapping evaluates the same samples in the same order on
+        # every layout (the automatic mapping may differ between layouts)
+        if mapping > 0:
+            for layout in (2, 3):
+                assert np.array_equal(results[layout, mapping][0], results[1, mapping][0])
         assert np.array_equal(results[1, mapping][1], results[1, 0][1])
 
 
@@ -204,7 +207,7 @@ def test_cell_view_follows_fusion(pf, case):
     poses = perturbed_poses(P, 256, 4.0, 4.0, seed=7)
     out = {}
     for layout in (1, 2, 3):
-        vol.set_fitness_variant(layout)
+        vol.set_fitness_variant(layout + 4)   # points on lanes: same order on every layout
         E, C = vol.fitness(to_dev(pts), to_dev(poses))
         out[layout] = (E.cpu().numpy(), C.cpu().numpy())
     assert np.count_nonzero(out[3][1]) > 100
