@@ -158,7 +158,7 @@ pf_status enqueue_backproject(const float* depth, const pf_intrinsics* intr, flo
 constexpr int FIT_THREADS = 256;
 constexpr int FIT_WARPS = FIT_THREADS / 32;
 constexpr int KC = 32;    // particles per CTA
-constexpr int PPT = 8;    // points per thread per sub-tile
+constexpr int PPT = 4;    // points per thread per sub-tile
 constexpr int SUBTILE = FIT_THREADS * PPT;
 
 enum Source { SRC_POSES = 0, SRC_SEARCH = 1, SRC_EVAL = 2 };
@@ -243,205 +243,46 @@ __device__ inline void compose_d(const double dR[9], const double dt[3], const d
         }
 }
 
-// A particle as the sampling loop uses it.  g = (A_hi + A_lo) x + b maps a
-// camera-frame point to grid units relative to an integer cell offset o: the
-// grid coordinate is g + o.  A = R / voxel carried as a float pair and
-// |b| < 1 make the transform as accurate as the FP64 pose it came from (the
-// rounding of a single float matrix would shift every point of a particle
-// the same way); the offset is folded into the cell bounds [lo, hi) and into
-// the magic constant of the floor, so it costs nothing per sample.
-struct Particle {      // shared memory, 128 bytes
-    float4 h0, h1, h2; // rows of A_hi | b
-    float4 l0, l1, l2; // rows of A_lo | lo bound
-    float4 u;          // hi bounds x y z | magic x
-    float4 m;          // magic y z | translation, rotation distance to the chunk's first particle
+// Particles as the sampling loop uses them.
+//
+// Particle k maps a camera-frame point x to grid units, relative to an
+// integer cell offset o_k, as g_k = A_k x + b_k with A_k = R_k / voxel and
+// b_k = (t_k - origin) / voxel - o_k in [0, 1).  The CTA splits
+// A_k = A_ref + dA_k, where A_ref is its first particle's matrix carried as a
+// float pair (hi + lo): y = A_ref x is formed once per point and shared by
+// all particles of the chunk, and each sample adds dA_k x + b_k in float.
+// dA_k is small (the particles of a chunk differ by the search size), so its
+// float rounding is negligible, and every sample position is as accurate as
+// the FP64 pose it came from; rounding a whole float matrix per particle
+// would instead shift all points of that particle alike.  The offset o_k is
+// folded into the magic constant of the floor and costs nothing per sample.
+struct Particle {      // shared memory, 64 bytes
+    float4 d0, d1, d2; // rows of dA_k | b_k
+    int4 m;            // magic x, y, z (cell offset folded in), unused
 };
 
 struct Xform {         // the same in registers
-    float a[9], l[9], b[3], lo[3], hi[3];
+    float d[9], b[3];
     int mg[3];
 };
 
 constexpr int kMagicBits = 0x4b400000;  // bits of 1.5 * 2^23
-
-// Grid-unit particle from a camera-to-world pose [R | t] given in FP64.
-__device__ inline void make_particle(const double R[9], const double t[3], const FitArgs& a, Particle& P)
-{
-    const double iv = 1.0 / a.vs;
-    const int n[3] = {a.nx, a.ny, a.nz};
-    float hi_[3][4], lo_[3][3], lob[3], hib[3];
-    int magic[3];
-    bool ok = true;
-    for (int r = 0; r < 3; ++r) {
-        const double tg = (t[r] - a.org[r]) * iv;
-        ok = ok && fabs(tg) < 2097152.0;  // 2^21: beyond, no point can reach the grid
-        const double o = ok ? floor(tg) : 0.0;
-        for (int c = 0; c < 3; ++c) {
-            const double Ag = R[3 * r + c] * iv;
-            const float h = (float)Ag;
-            hi_[r][c] = h;
-            lo_[r][c] = (float)(Ag - (double)h);
-        }
-        hi_[r][3] = (float)(tg - o);
-        lob[r] = (float)(-o);
-        hib[r] = (float)((double)(n[r] - 1) - o);
-        magic[r] = kMagicBits - (int)o;
-    }
-    if (!ok)
-        for (int r = 0; r < 3; ++r) {
-            lob[r] = 1.0f;
-            hib[r] = 0.0f;
-        }
-    P.h0 = make_float4(hi_[0][0], hi_[0][1], hi_[0][2], hi_[0][3]);
-    P.h1 = make_float4(hi_[1][0], hi_[1][1], hi_[1][2], hi_[1][3]);
-    P.h2 = make_float4(hi_[2][0], hi_[2][1], hi_[2][2], hi_[2][3]);
-    P.l0 = make_float4(lo_[0][0], lo_[0][1], lo_[0][2], lob[0]);
-    P.l1 = make_float4(lo_[1][0], lo_[1][1], lo_[1][2], lob[1]);
-    P.l2 = make_float4(lo_[2][0], lo_[2][1], lo_[2][2], lob[2]);
-    P.u = make_float4(hib[0], hib[1], hib[2], __int_as_float(magic[0]));
-    P.m = make_float4(__int_as_float(magic[1]), __int_as_float(magic[2]), 0.0f, 0.0f);
-}
+constexpr int kNeverValid = 0x7fffffff;  // magic of a particle that reaches no cell
 
 __device__ __forceinline__ void load_xform(const Particle& P, Xform& X)
 {
-    const float4 h0 = P.h0, h1 = P.h1, h2 = P.h2, l0 = P.l0, l1 = P.l1, l2 = P.l2, u = P.u, m = P.m;
-    X.a[0] = h0.x; X.a[1] = h0.y; X.a[2] = h0.z; X.b[0] = h0.w;
-    X.a[3] = h1.x; X.a[4] = h1.y; X.a[5] = h1.z; X.b[1] = h1.w;
-    X.a[6] = h2.x; X.a[7] = h2.y; X.a[8] = h2.z; X.b[2] = h2.w;
-    X.l[0] = l0.x; X.l[1] = l0.y; X.l[2] = l0.z; X.lo[0] = l0.w;
-    X.l[3] = l1.x; X.l[4] = l1.y; X.l[5] = l1.z; X.lo[1] = l1.w;
-    X.l[6] = l2.x; X.l[7] = l2.y; X.l[8] = l2.z; X.lo[2] = l2.w;
-    X.hi[0] = u.x; X.hi[1] = u.y; X.hi[2] = u.z; X.mg[0] = __float_as_int(u.w);
-    X.mg[1] = __float_as_int(m.x); X.mg[2] = __float_as_int(m.y);
+    const float4 d0 = P.d0, d1 = P.d1, d2 = P.d2;
+    const int4 m = P.m;
+    X.d[0] = d0.x; X.d[1] = d0.y; X.d[2] = d0.z; X.b[0] = d0.w;
+    X.d[3] = d1.x; X.d[4] = d1.y; X.d[5] = d1.z; X.b[1] = d1.w;
+    X.d[6] = d2.x; X.d[7] = d2.y; X.d[8] = d2.z; X.b[2] = d2.w;
+    X.mg[0] = m.x; X.mg[1] = m.y; X.mg[2] = m.z;
 }
 
-// Grid coordinates (relative to the particle's cell offset) of a point:
-// the small A_lo terms and b first, then A_hi.
-__device__ __forceinline__ void apply(const Xform& X, float x, float y, float z, float& gx, float& gy, float& gz)
-{
-    gx = fmaf(X.a[0], x, fmaf(X.a[1], y, fmaf(X.a[2], z, fmaf(X.l[0], x, fmaf(X.l[1], y, fmaf(X.l[2], z, X.b[0]))))));
-    gy = fmaf(X.a[3], x, fmaf(X.a[4], y, fmaf(X.a[5], z, fmaf(X.l[3], x, fmaf(X.l[4], y, fmaf(X.l[5], z, X.b[1]))))));
-    gz = fmaf(X.a[6], x, fmaf(X.a[7], y, fmaf(X.a[8], z, fmaf(X.l[6], x, fmaf(X.l[7], y, fmaf(X.l[8], z, X.b[2]))))));
-}
-
-// Fast-path sample: tsdf only.  Non-finite nodes (unobserved or outside the
-// band) make the interpolated value non-finite, so the validity test of the
-// cell is a single comparison on the result.
-__device__ __forceinline__ void sample_encoded(const float* __restrict__ tsdf, int nx, int nxy, const Xform& X,
-                                               float gx, float gy, float gz, float& s, int& c)
-{
-    if (gx >= X.lo[0] && gx < X.hi[0] && gy >= X.lo[1] && gy < X.hi[1] && gz >= X.lo[2] && gz < X.hi[2]) {
-        // floor(g) for |g| < 2^22: adding 1.5*2^23 rounding down leaves
-        // floor(g) in the low mantissa bits and keeps every step exact; the
-        // particle's magic constant also adds its integer cell offset
-        const float M = 12582912.0f;
-        const float rx = __fadd_rd(gx, M), ry = __fadd_rd(gy, M), rz = __fadd_rd(gz, M);
-        const int ix = __float_as_int(rx) - X.mg[0];
-        const int iy = __float_as_int(ry) - X.mg[1];
-        const int iz = __float_as_int(rz) - X.mg[2];
-        const float fx = gx - (rx - M), fy = gy - (ry - M), fz = gz - (rz - M);
-        const float* p = tsdf + (ix + nx * iy + nxy * iz);
-        const float v000 = __ldg(p), v100 = __ldg(p + 1);
-        const float v010 = __ldg(p + nx), v110 = __ldg(p + nx + 1);
-        const float v001 = __ldg(p + nxy), v101 = __ldg(p + nxy + 1);
-        const float v011 = __ldg(p + nxy + nx), v111 = __ldg(p + nxy + nx + 1);
-        const float x00 = fmaf(fx, v100 - v000, v000);
-        const float x10 = fmaf(fx, v110 - v010, v010);
-        const float x01 = fmaf(fx, v101 - v001, v001);
-        const float x11 = fmaf(fx, v111 - v011, v011);
-        const float y0 = fmaf(fy, x10 - x00, x00);
-        const float y1 = fmaf(fy, x11 - x01, x01);
-        const float t = fabsf(fmaf(fz, y1 - y0, y0));
-        if (t < INFINITY) {
-            s += t;
-            c += 1;
-        }
-    }
-}
-
-// Plain sample: tsdf and weight, all eight nodes tested explicitly.
-__device__ __forceinline__ void sample_plain(const float* __restrict__ tsdf, const float* __restrict__ weight, int nx,
-                                             int nxy, const Xform& X, float gx, float gy, float gz, float& s, int& c)
-{
-    if (gx >= X.lo[0] && gx < X.hi[0] && gy >= X.lo[1] && gy < X.hi[1] && gz >= X.lo[2] && gz < X.hi[2]) {
-        const float M = 12582912.0f;
-        const float rx = __fadd_rd(gx, M), ry = __fadd_rd(gy, M), rz = __fadd_rd(gz, M);
-        const int base = (__float_as_int(rx) - X.mg[0]) + nx * (__float_as_int(ry) - X.mg[1]) +
-                         nxy * (__float_as_int(rz) - X.mg[2]);
-        const float fx = gx - (rx - M), fy = gy - (ry - M), fz = gz - (rz - M);
-        const int off[8] = {0, 1, nx, nx + 1, nxy, nxy + 1, nxy + nx, nxy + nx + 1};
-        float v[8];
-        bool ok = true;
-#pragma unroll
-        for (int q = 0; q < 8; ++q) {
-            const float w = __ldg(weight + base + off[q]);
-            v[q] = __ldg(tsdf + base + off[q]);
-            ok = ok && (w > 0.0f) && (fabsf(v[q]) < 1.0f);
-        }
-        if (ok) {
-            const float x00 = fmaf(fx, v[1] - v[0], v[0]);
-            const float x10 = fmaf(fx, v[3] - v[2], v[2]);
-            const float x01 = fmaf(fx, v[5] - v[4], v[4]);
-            const float x11 = fmaf(fx, v[7] - v[6], v[6]);
-            const float y0 = fmaf(fy, x10 - x00, x00);
-            const float y1 = fmaf(fy, x11 - x01, x01);
-            s += fabsf(fmaf(fz, y1 - y0, y0));
-            c += 1;
-        }
-    }
-}
-
-// Cell-view sample: the eight corners of the cell are one 32-byte sector,
-// fetched as two 16-byte loads; same arithmetic as sample_encoded.
-__device__ __forceinline__ void sample_cells(const float4* __restrict__ cells, int nx, int nxy, const Xform& X,
-                                             float gx, float gy, float gz, float& s, int& c)
-{
-    if (gx >= X.lo[0] && gx < X.hi[0] && gy >= X.lo[1] && gy < X.hi[1] && gz >= X.lo[2] && gz < X.hi[2]) {
-        const float M = 12582912.0f;
-        const float rx = __fadd_rd(gx, M), ry = __fadd_rd(gy, M), rz = __fadd_rd(gz, M);
-        const int idx = (__float_as_int(rx) - X.mg[0]) + nx * (__float_as_int(ry) - X.mg[1]) +
-                        nxy * (__float_as_int(rz) - X.mg[2]);
-        const float fx = gx - (rx - M), fy = gy - (ry - M), fz = gz - (rz - M);
-        const float4* p = cells + 2 * (size_t)idx;
-        const float4 lo = __ldg(p), hi = __ldg(p + 1);
-        const float x00 = fmaf(fx, lo.y - lo.x, lo.x);
-        const float x10 = fmaf(fx, lo.w - lo.z, lo.z);
-        const float x01 = fmaf(fx, hi.y - hi.x, hi.x);
-        const float x11 = fmaf(fx, hi.w - hi.z, hi.z);
-        const float y0 = fmaf(fy, x10 - x00, x00);
-        const float y1 = fmaf(fy, x11 - x01, x01);
-        const float t = fabsf(fmaf(fz, y1 - y0, y0));
-        if (t < INFINITY) {
-            s += t;
-            c += 1;
-        }
-    }
-}
-
-// VARIANT: 0 encoded tsdf nodes, 1 plain (tsdf + weight), 2 cell view.
-template <int VARIANT>
-__device__ __forceinline__ void sample(const FitArgs& a, int nx, int nxy, const Xform& X, float x, float y, float z,
-                                       float& s, int& c)
-{
-    float gx, gy, gz;
-    apply(X, x, y, z, gx, gy, gz);
-    if (VARIANT == 0)
-        sample_encoded(a.tsdf, nx, nxy, X, gx, gy, gz, s, c);
-    else if (VARIANT == 1)
-        sample_plain(a.tsdf, a.weight, nx, nxy, X, gx, gy, gz, s, c);
-    else
-        sample_cells(a.cells, nx, nxy, X, gx, gy, gz, s, c);
-}
-
-// Particles k_begin .. k_begin+kc-1 of this launch into shared memory, in FP64
-// (the search composes dP_k * P exactly as the pose update does).
+// Camera-to-world pose of particle k in FP64.
 template <int SRC>
-__device__ void build_particles(const FitArgs& a, int k_begin, int kc, Particle* sP)
+__device__ inline void particle_pose(const FitArgs& a, int k, double R[9], double tw[3])
 {
-    const int t = threadIdx.x;
-    if (t >= kc) return;
-    const int k = k_begin + t;
-    double R[9], tw[3];
     if (SRC == SRC_POSES) {
         const float* p = a.poses + 12 * (size_t)k;
         for (int r = 0; r < 3; ++r) {
@@ -470,7 +311,163 @@ __device__ void build_particles(const FitArgs& a, int k_begin, int kc, Particle*
             }
         }
     }
-    make_particle(R, tw, a, sP[t]);
+}
+
+// Particles k_begin .. k_begin+kc-1 into shared memory, and the chunk's
+// reference matrix A_ref (its first particle) as hi and lo floats.
+template <int SRC>
+__device__ void build_particles(const FitArgs& a, int k_begin, int kc, Particle* sP, float* sRef)
+{
+    const int t = threadIdx.x;
+    if (t >= kc) return;
+    double R[9], tw[3], R0[9], t0[3];
+    particle_pose<SRC>(a, k_begin + t, R, tw);
+    particle_pose<SRC>(a, k_begin, R0, t0);
+    const double iv = 1.0 / a.vs;
+    float d[9], b[3];
+    int magic[3];
+    bool ok = true;
+    for (int r = 0; r < 3; ++r) {
+        for (int c = 0; c < 3; ++c) d[3 * r + c] = (float)(R[3 * r + c] * iv - R0[3 * r + c] * iv);
+        const double tg = (tw[r] - a.org[r]) * iv;
+        ok = ok && fabs(tg) < 2097152.0;  // 2^21: beyond, no point can reach the grid
+        const double o = ok ? floor(tg) : 0.0;
+        b[r] = (float)(tg - o);
+        magic[r] = kMagicBits - (int)o;
+    }
+    if (!ok) magic[0] = kNeverValid;
+    sP[t].d0 = make_float4(d[0], d[1], d[2], b[0]);
+    sP[t].d1 = make_float4(d[3], d[4], d[5], b[1]);
+    sP[t].d2 = make_float4(d[6], d[7], d[8], b[2]);
+    sP[t].m = make_int4(magic[0], magic[1], magic[2], 0);
+    if (t == 0)
+        for (int q = 0; q < 9; ++q) {
+            const double A0 = R0[q] * iv;
+            const float hi = (float)A0;
+            sRef[q] = hi;
+            sRef[9 + q] = (float)(A0 - (double)hi);
+        }
+}
+
+// One row of y = A_ref x, with A_ref = hi + lo, accurate to ~1e-12 of |y|
+// (exact products and two-sums in float), returned as an integer part and a
+// fraction: y = yi + yf with |yf| <= ~0.5.  Done once per point per block of
+// points and shared by every particle of the chunk, so each sample only
+// rounds at the scale of dA_k x + yf + b_k (a few voxels) rather than at the
+// scale of the grid coordinate itself.
+__device__ __forceinline__ void ref_row(const float* hi, const float* lo, float x, float y, float z, int& yi, float& yf)
+{
+    const float p0 = hi[0] * x, p1 = hi[1] * y, p2 = hi[2] * z;
+    float err = fmaf(hi[0], x, -p0) + fmaf(hi[1], y, -p1) + fmaf(hi[2], z, -p2);
+    const float s1 = p0 + p1;
+    float bb = s1 - p0;
+    err += (p0 - (s1 - bb)) + (p1 - bb);
+    const float s2 = s1 + p2;
+    bb = s2 - s1;
+    err += (s1 - (s2 - bb)) + (p2 - bb);
+    err = fmaf(lo[0], x, fmaf(lo[1], y, fmaf(lo[2], z, err)));
+    const float r = rintf(s2);
+    yi = __float2int_rn(r);
+    yf = (s2 - r) + err;
+}
+
+__device__ __forceinline__ void ref_apply(const float* Rf, float x, float y, float z, int* Yi, float* Yf)
+{
+    ref_row(Rf + 0, Rf + 9, x, y, z, Yi[0], Yf[0]);
+    ref_row(Rf + 3, Rf + 12, x, y, z, Yi[1], Yf[1]);
+    ref_row(Rf + 6, Rf + 15, x, y, z, Yi[2], Yf[2]);
+}
+
+// Grid cell and fractions of a sample.  The grid coordinate is
+// o_k + yi + (dA_k x + yf + b_k); the bracket is small and its floor comes
+// from adding 1.5*2^23 rounding down, which leaves floor() in the low
+// mantissa bits with every step exact (for |.| < 2^22).  Subtracting the
+// particle's magic constant adds o_k, and yi is added in the same integer
+// instruction.  Any coordinate outside [0, n-1), including NaN, gives an
+// index outside that range on some axis (huge values wrap far outside), so
+// one unsigned compare per axis is the whole range test.
+struct Cell {
+    int idx;
+    float fx, fy, fz;
+    bool ok;
+};
+
+__device__ __forceinline__ Cell locate(const Xform& X, int nx, int nxy, unsigned mx, unsigned my, unsigned mz,
+                                       float x, float y, float z, const int* Yi, const float* Yf)
+{
+    const float gx = fmaf(X.d[0], x, fmaf(X.d[1], y, fmaf(X.d[2], z, Yf[0] + X.b[0])));
+    const float gy = fmaf(X.d[3], x, fmaf(X.d[4], y, fmaf(X.d[5], z, Yf[1] + X.b[1])));
+    const float gz = fmaf(X.d[6], x, fmaf(X.d[7], y, fmaf(X.d[8], z, Yf[2] + X.b[2])));
+    const float M = 12582912.0f;
+    const float rx = __fadd_rd(gx, M), ry = __fadd_rd(gy, M), rz = __fadd_rd(gz, M);
+    const int ix = __float_as_int(rx) - X.mg[0] + Yi[0];
+    const int iy = __float_as_int(ry) - X.mg[1] + Yi[1];
+    const int iz = __float_as_int(rz) - X.mg[2] + Yi[2];
+    Cell c;
+    c.ok = (unsigned)ix < mx && (unsigned)iy < my && (unsigned)iz < mz;
+    c.idx = ix + nx * iy + nxy * iz;
+    c.fx = gx - (rx - M);
+    c.fy = gy - (ry - M);
+    c.fz = gz - (rz - M);
+    return c;
+}
+
+__device__ __forceinline__ void accumulate(float t, float& s, int& c)
+{
+    t = fabsf(t);
+    if (t < INFINITY) {  // non-finite: some corner unobserved or outside the band
+        s += t;
+        c += 1;
+    }
+}
+
+__device__ __forceinline__ float trilerp(float fx, float fy, float fz, float v000, float v100, float v010, float v110,
+                                         float v001, float v101, float v011, float v111)
+{
+    const float x00 = fmaf(fx, v100 - v000, v000);
+    const float x10 = fmaf(fx, v110 - v010, v010);
+    const float x01 = fmaf(fx, v101 - v001, v001);
+    const float x11 = fmaf(fx, v111 - v011, v011);
+    const float y0 = fmaf(fy, x10 - x00, x00);
+    const float y1 = fmaf(fy, x11 - x01, x01);
+    return fmaf(fz, y1 - y0, y0);
+}
+
+// One sample.  VARIANT 0: encoded tsdf nodes (non-finite nodes make the
+// interpolated value non-finite, so validity is one comparison on the
+// result); 1: plain tsdf + weight, all eight nodes tested explicitly;
+// 2: the cell view, whose eight corners are one 32-byte sector.
+template <int VARIANT>
+__device__ __forceinline__ void sample(const FitArgs& a, int nx, int nxy, unsigned mx, unsigned my, unsigned mz,
+                                       const Xform& X, float x, float y, float z, const int* Yi, const float* Yf,
+                                       float& s, int& c)
+{
+    const Cell q = locate(X, nx, nxy, mx, my, mz, x, y, z, Yi, Yf);
+    if (!q.ok) return;
+    if (VARIANT == 2) {
+        const float4* p = a.cells + 2 * (size_t)q.idx;
+        const float4 lo = __ldg(p), hi = __ldg(p + 1);
+        accumulate(trilerp(q.fx, q.fy, q.fz, lo.x, lo.y, lo.z, lo.w, hi.x, hi.y, hi.z, hi.w), s, c);
+    } else if (VARIANT == 0) {
+        const float* p = a.tsdf + q.idx;
+        accumulate(trilerp(q.fx, q.fy, q.fz, __ldg(p), __ldg(p + 1), __ldg(p + nx), __ldg(p + nx + 1), __ldg(p + nxy),
+                           __ldg(p + nxy + 1), __ldg(p + nxy + nx), __ldg(p + nxy + nx + 1)),
+                   s, c);
+    } else {
+        const int off[8] = {0, 1, nx, nx + 1, nxy, nxy + 1, nxy + nx, nxy + nx + 1};
+        float v[8];
+        bool ok = true;
+#pragma unroll
+        for (int r = 0; r < 8; ++r) {
+            const float w = __ldg(a.weight + q.idx + off[r]);
+            v[r] = __ldg(a.tsdf + q.idx + off[r]);
+            ok = ok && (w > 0.0f) && (fabsf(v[r]) < 1.0f);
+        }
+        if (ok) {
+            s += fabsf(trilerp(q.fx, q.fy, q.fz, v[0], v[1], v[2], v[3], v[4], v[5], v[6], v[7]));
+            c += 1;
+        }
+    }
 }
 
 // Block-wide argmin of (E, k) with the lowest k among equal E.
@@ -503,10 +500,18 @@ __device__ inline void argmin_pair(float& e, int& k, float* se, int* sk)
     __syncthreads();
 }
 
+#ifndef PF_FIT_MIN_BLOCKS
+#define PF_FIT_MIN_BLOCKS 3
+#endif
+
 template <int SRC, int VARIANT>
-__global__ void __launch_bounds__(FIT_THREADS, 3) fitness_kernel(FitArgs a)
+__global__ void __launch_bounds__(FIT_THREADS, PF_FIT_MIN_BLOCKS) fitness_kernel(FitArgs a)
 {
     __shared__ Particle sP[KC];
+    __shared__ float sRef[18];
+    // particles-on-lanes: each warp's points: (x, y, z, yi.x), (yf, yi.y), yi.z
+    __shared__ float4 sPts[FIT_WARPS][PPT * 32][2];
+    __shared__ int sYz[FIT_WARPS][PPT * 32];
     __shared__ float accS[FIT_WARPS][KC];
     __shared__ int accC[FIT_WARPS][KC];
     __shared__ int s_last;
@@ -533,26 +538,24 @@ __global__ void __launch_bounds__(FIT_THREADS, 3) fitness_kernel(FitArgs a)
     }
     __syncthreads();
     const bool skip = s_skip != 0;
-    if (!skip) build_particles<SRC>(a, k_begin, kc, sP);
+    if (!skip) build_particles<SRC>(a, k_begin, kc, sP, sRef);
     __syncthreads();
-    // spread of the chunk's particles: translation (voxels) and rotation
-    // (voxels per metre) relative to its first particle
+    // spread of the chunk's particles relative to its first one: translation
+    // (voxels) and rotation (voxels per metre of point distance)
     if (tid == 0) {
         float dt = 0.0f, dr = 0.0f;
         if (!skip) {
-            const Particle& P0 = sP[0];
-            const float o0[3] = {(float)(kMagicBits - __float_as_int(P0.u.w)), (float)(kMagicBits - __float_as_int(P0.m.x)),
-                                 (float)(kMagicBits - __float_as_int(P0.m.y))};
+            const float o0[3] = {(float)(kMagicBits - sP[0].m.x), (float)(kMagicBits - sP[0].m.y),
+                                 (float)(kMagicBits - sP[0].m.z)};
+            const float b0[3] = {sP[0].d0.w, sP[0].d1.w, sP[0].d2.w};
             for (int k = 1; k < kc; ++k) {
                 const Particle& P = sP[k];
-                const float ok_[3] = {(float)(kMagicBits - __float_as_int(P.u.w)), (float)(kMagicBits - __float_as_int(P.m.x)),
-                                      (float)(kMagicBits - __float_as_int(P.m.y))};
-                dt = fmaxf(dt, fabsf((ok_[0] + P.h0.w) - (o0[0] + P0.h0.w)));
-                dt = fmaxf(dt, fabsf((ok_[1] + P.h1.w) - (o0[1] + P0.h1.w)));
-                dt = fmaxf(dt, fabsf((ok_[2] + P.h2.w) - (o0[2] + P0.h2.w)));
-                dr = fmaxf(dr, fabsf(P.h0.x - P0.h0.x) + fabsf(P.h0.y - P0.h0.y) + fabsf(P.h0.z - P0.h0.z));
-                dr = fmaxf(dr, fabsf(P.h1.x - P0.h1.x) + fabsf(P.h1.y - P0.h1.y) + fabsf(P.h1.z - P0.h1.z));
-                dr = fmaxf(dr, fabsf(P.h2.x - P0.h2.x) + fabsf(P.h2.y - P0.h2.y) + fabsf(P.h2.z - P0.h2.z));
+                dt = fmaxf(dt, fabsf((float)(kMagicBits - P.m.x) + P.d0.w - (o0[0] + b0[0])));
+                dt = fmaxf(dt, fabsf((float)(kMagicBits - P.m.y) + P.d1.w - (o0[1] + b0[1])));
+                dt = fmaxf(dt, fabsf((float)(kMagicBits - P.m.z) + P.d2.w - (o0[2] + b0[2])));
+                dr = fmaxf(dr, fabsf(P.d0.x) + fabsf(P.d0.y) + fabsf(P.d0.z));
+                dr = fmaxf(dr, fabsf(P.d1.x) + fabsf(P.d1.y) + fabsf(P.d1.z));
+                dr = fmaxf(dr, fabsf(P.d2.x) + fabsf(P.d2.y) + fabsf(P.d2.z));
             }
         }
         s_spread[0] = dt;
@@ -565,10 +568,15 @@ __global__ void __launch_bounds__(FIT_THREADS, 3) fitness_kernel(FitArgs a)
     const long long beg = Ne * blockIdx.y / a.n_ptiles;
     const long long end = Ne * (blockIdx.y + 1) / a.n_ptiles;
     const int nx = a.nx, nxy = a.nx * a.ny;
+    const unsigned mx = a.nx - 1, my = a.ny - 1, mz = a.nz - 1;
 
     if (!skip) {
+        float Rf[18];
+#pragma unroll
+        for (int q = 0; q < 18; ++q) Rf[q] = sRef[q];
         for (long long sub = beg; sub < end; sub += SUBTILE) {
-            float px[PPT], py[PPT], pz[PPT];
+            float px[PPT], py[PPT], pz[PPT], Yf[PPT][3];
+            int Yi[PPT][3];
             float r2 = 0.0f;
 #pragma unroll
             for (int p = 0; p < PPT; ++p) {
@@ -584,6 +592,7 @@ __global__ void __launch_bounds__(FIT_THREADS, 3) fitness_kernel(FitArgs a)
                     py[p] = NAN;
                     pz[p] = NAN;
                 }
+                ref_apply(Rf, px[p], py[p], pz[p], Yi[p], Yf[p]);
             }
             // mapping of this sub-tile: when every particle puts a point in
             // (nearly) the same cell, lanes take particles and share a point,
@@ -606,7 +615,8 @@ __global__ void __launch_bounds__(FIT_THREADS, 3) fitness_kernel(FitArgs a)
                     float s = 0.0f;
                     int c = 0;
 #pragma unroll
-                    for (int p = 0; p < PPT; ++p) sample<VARIANT>(a, nx, nxy, X, px[p], py[p], pz[p], s, c);
+                    for (int p = 0; p < PPT; ++p)
+                        sample<VARIANT>(a, nx, nxy, mx, my, mz, X, px[p], py[p], pz[p], Yi[p], Yf[p], s, c);
 #pragma unroll
                     for (int o = 16; o > 0; o >>= 1) {
                         s += __shfl_xor_sync(0xffffffffu, s, o);
@@ -618,19 +628,26 @@ __global__ void __launch_bounds__(FIT_THREADS, 3) fitness_kernel(FitArgs a)
                     }
                 }
             } else {
+#pragma unroll
+                for (int p = 0; p < PPT; ++p) {
+                    sPts[warp][p * 32 + lane][0] = make_float4(px[p], py[p], pz[p], __int_as_float(Yi[p][0]));
+                    sPts[warp][p * 32 + lane][1] = make_float4(Yf[p][0], Yf[p][1], Yf[p][2], __int_as_float(Yi[p][1]));
+                    sYz[warp][p * 32 + lane] = Yi[p][2];
+                }
+                __syncwarp();
                 Xform X;
                 load_xform(sP[lane < kc ? lane : 0], X);
                 float s = 0.0f;
                 int c = 0;
-#pragma unroll
-                for (int p = 0; p < PPT; ++p) {
-                    for (int j = 0; j < 32; ++j) {
-                        const float x = __shfl_sync(0xffffffffu, px[p], j);
-                        const float y = __shfl_sync(0xffffffffu, py[p], j);
-                        const float z = __shfl_sync(0xffffffffu, pz[p], j);
-                        sample<VARIANT>(a, nx, nxy, X, x, y, z, s, c);
-                    }
+#pragma unroll 2
+                for (int q = 0; q < PPT * 32; ++q) {
+                    const float4 xp = sPts[warp][q][0];
+                    const float4 yp = sPts[warp][q][1];
+                    const int yi[3] = {__float_as_int(xp.w), __float_as_int(yp.w), sYz[warp][q]};
+                    const float yf[3] = {yp.x, yp.y, yp.z};
+                    sample<VARIANT>(a, nx, nxy, mx, my, mz, X, xp.x, xp.y, xp.z, yi, yf, s, c);
                 }
+                __syncwarp();
                 if (lane < kc) {
                     accS[warp][lane] += s;
                     accC[warp][lane] += c;
