@@ -194,6 +194,26 @@ PF_API pf_status pf_backproject(const float* depth_dev, const pf_intrinsics* int
 PF_API pf_status pf_fitness(const pf_volume* vol, const float* points_dev, int n, const float* poses_dev,
                      int k, float* fitness_dev, int* count_dev, void* cuda_stream);
 
+/* As pf_fitness, but allocates no device memory (no cudaMalloc, no library
+ * allocator), for callers that must not allocate once they are running --
+ * e.g. a process whose device memory is owned by another allocator, or a
+ * real-time loop that cannot afford the device-wide synchronisation an
+ * allocation implies.  The paper has no counterpart: this is an interface
+ * variant of pf_fitness, with identical semantics and arguments.
+ *   Scratch: the kernel's partial sums live in one fixed array of
+ *   PF_NOALLOC_MAX_SLOTS (point tile, pose) slots (about 512 KiB) that every
+ *   device which loads the library holds until the process exits.
+ *   k > PF_NOALLOC_MAX_SLOTS is rejected with PF_ERR_INVALID_ARG before
+ *   anything is enqueued; smaller k may use fewer point tiles than
+ *   pf_fitness, which changes only the float summation order.
+ *   The first call on a device looks up the array's device address (set-up,
+ *   once per device); make that first call before any stream capture.
+ *   All calls share the array: calls that overlap on the GPU (other streams,
+ *   other host threads) race and must be serialised by the caller. */
+#define PF_NOALLOC_MAX_SLOTS 65536
+PF_API pf_status pf_fitness_noalloc(const pf_volume* vol, const float* points_dev, int n, const float* poses_dev,
+                                    int k, float* fitness_dev, int* count_dev, void* cuda_stream);
+
 /* Randomized pose optimization of one frame (Sec. III-B): back-projects the
  * depth, then runs params->n_iters iterations of sample / evaluate / select /
  * update, starting from init_pose with search size (init_rot_deg,

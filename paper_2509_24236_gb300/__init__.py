@@ -62,7 +62,7 @@ class pf_track_stats(C.Structure):
 
 
 EXPORTS = ["pf_create_volume", "pf_destroy_volume", "pf_reset_volume", "pf_volume_upload", "pf_volume_download",
-           "pf_integrate", "pf_integrate_async", "pf_pose_compose", "pf_backproject", "pf_fitness", "pf_track_frame", "pf_track_frame_async",
+           "pf_integrate", "pf_integrate_async", "pf_pose_compose", "pf_backproject", "pf_fitness", "pf_fitness_noalloc", "pf_track_frame", "pf_track_frame_async",
            "pf_track_reserve", "pf_raycast", "pf_set_fitness_variant", "pf_status_string", "pf_launch_count",
            "pf_set_kernel_timing", "pf_kernel_timing"]
 
@@ -97,6 +97,7 @@ def load(path: str = LIB_PATH):
         "pf_pose_compose": (st, [vp, vp, vp, vp]),
         "pf_backproject": (st, [vp, C.POINTER(pf_intrinsics), vp, C.c_int, vp, vp]),
         "pf_fitness": (st, [vp, vp, C.c_int, vp, C.c_int, vp, vp, vp]),
+        "pf_fitness_noalloc": (st, [vp, vp, C.c_int, vp, C.c_int, vp, vp, vp]),
         "pf_track_frame": (st, [vp, vp, C.POINTER(pf_intrinsics), C.POINTER(pf_track_params), dp, dp,
                                 C.POINTER(pf_track_stats), vp]),
         "pf_track_frame_async": (st, [vp, vp, C.POINTER(pf_intrinsics), C.POINTER(pf_track_params), vp, vp,
@@ -225,6 +226,18 @@ def pf_fitness(vol, points, n: int, poses, k: int, fitness, count, stream=None) 
     return _check(load().pf_fitness(vol, _dptr(points, torch.float32) if n > 0 else None, n,
                                     _dptr(poses, torch.float32), k, _dptr(fitness, torch.float32),
                                     _dptr(count, torch.int32), _stream(stream)), "pf_fitness")
+
+
+PF_NOALLOC_MAX_SLOTS = 65536
+
+
+def pf_fitness_noalloc(vol, points, n: int, poses, k: int, fitness, count, stream=None) -> int:
+    """pf_fitness without any device allocation (fixed scratch inside the
+    library; calls must not overlap on the GPU).  Returns the pf_status."""
+    import torch
+    return load().pf_fitness_noalloc(vol, _dptr(points, torch.float32) if n > 0 else None, n,
+                                     _dptr(poses, torch.float32), k, _dptr(fitness, torch.float32),
+                                     _dptr(count, torch.int32), _stream(stream))
 
 
 def pf_track_frame(vol, depth, intr, params: pf_track_params, init_pose, stream=None):

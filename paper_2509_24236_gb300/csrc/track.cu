@@ -31,6 +31,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <mutex>
 
 #include "pf_internal.cuh"
 
@@ -1163,3 +1164,87 @@ pf_status pf_track_frame(pf_volume* v, const float* depth_dev, const pf_intrinsi
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Fitness without any device allocation.
+//
+// pf_fitness keeps its per-tile partial sums in the volume's workspace and
+// grows it with cudaMalloc when a call needs more.  Callers that must not
+// allocate device memory once they are running -- for instance a process
+// whose device memory is owned by another allocator, or a real-time loop
+// that cannot afford the device-wide synchronisation a cudaMalloc implies --
+// use pf_fitness_noalloc instead: the same kernel, with its scratch (the
+// partial sums and the ticket counter of the last-block reduction) in the
+// fixed array below, which every device that loads the library holds until
+// the process exits.
+// ---------------------------------------------------------------------------
+namespace {
+
+struct NoAllocScratch {
+    unsigned int counter;              // ticket counter; must be zero when a launch starts
+    unsigned int pad[63];
+    float S[PF_NOALLOC_MAX_SLOTS];     // partial sums, one per (point tile, pose)
+    int C[PF_NOALLOC_MAX_SLOTS];       // partial counts
+};
+
+static __device__ __align__(256) NoAllocScratch g_noalloc_scratch;
+
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mu;
+NoAllocScratch* g_noalloc_addr[kMaxDevices] = {};
+
+// Device address of the scratch array on the current device, looked up once
+// per device (the first call on a device does this set-up).
+pf_status noalloc_scratch(NoAllocScratch** out)
+{
+    int dev = 0;
+    PF_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kMaxDevices) return PF_ERR_UNSUPPORTED;
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_addr[dev]) {
+        void* p = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) return pf::cuda_status(e);
+        if (!p) return PF_ERR_CUDA;
+        g_noalloc_addr[dev] = static_cast<NoAllocScratch*>(p);
+    }
+    *out = g_noalloc_addr[dev];
+    return PF_OK;
+}
+
+}  // namespace
+
+extern "C" pf_status pf_fitness_noalloc(const pf_volume* v, const float* points_dev, int n, const float* poses_dev,
+                                        int k, float* fitness_dev, int* count_dev, void* stream)
+{
+    if (!v || !poses_dev || !fitness_dev || !count_dev) return PF_ERR_INVALID_ARG;
+    if (n < 0 || k < 1 || (n > 0 && !points_dev)) return PF_ERR_INVALID_ARG;
+    if (k > PF_NOALLOC_MAX_SLOTS) return PF_ERR_INVALID_ARG;  // more poses than the scratch holds
+    NoAllocScratch* sc = nullptr;
+    pf_status st = noalloc_scratch(&sc);
+    if (st != PF_OK) return st;
+    const int chunks = (k + KC - 1) / KC;
+    // as many point tiles as pf_fitness would use, within the fixed scratch
+    const int tiles = std::max(1, std::min(choose_ptiles(v->device, chunks, n), PF_NOALLOC_MAX_SLOTS / k));
+    FitArgs a;
+    memset(&a, 0, sizeof(a));
+    a.pts = reinterpret_cast<const float4*>(points_dev);
+    a.n_dev = nullptr;
+    a.n_host = n;
+    a.stride = 1;
+    a.K = k;
+    a.poses = poses_dev;
+    fill_volume_args(a, v);
+    a.part_S = sc->S;
+    a.part_C = sc->C;
+    a.counter = &sc->counter;
+    a.n_ptiles = tiles;
+    a.out_E = fitness_dev;
+    a.out_C = count_dev;
+    cudaStream_t s = (cudaStream_t)stream;
+    // the array keeps the previous call's contents: the counter must start at zero
+    PF_CUDA(cudaMemsetAsync(&sc->counter, 0, sizeof(unsigned int), s));
+    launch_fitness<SRC_POSES>(a, v->fitness_variant, v->cells != nullptr, chunks, s);
+    PF_LAUNCHED();
+    return PF_OK;
+}
