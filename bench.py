@@ -57,6 +57,11 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ref-particles", type=int, default=192,
                     help="particles per reference-arm step (a bounded slice of one iteration)")
+    ap.add_argument("--kernel", default=None, choices=["fitness", "integrate"],
+                    help="time one kernel on the multiroom volume instead of the frame loop (profiling)")
+    ap.add_argument("--spread", type=float, default=3.0,
+                    help="--kernel fitness: poses perturbed up to this many degrees and centimetres")
+    ap.add_argument("--reps", type=int, default=3, help="--kernel: timed launches after one warm-up launch")
     return ap.parse_args()
 
 
@@ -189,8 +194,38 @@ def oracle_sample(seq, depths, rels, compose_mode: int, n_particles: int, repeat
     return 1.0 / t_frame, desc, oracle.num_threads(), times, t_int, pts.shape[0]
 
 
+# ---------------------------------------------------------------------------
+# ranks (replicas: one independent sequence per GPU, no data-path collective)
+# ---------------------------------------------------------------------------
+
+def world_info():
+    """(world size, rank, local rank) from the torchrun environment."""
+    return (int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+def replica_seed(base_seed: int, rank: int) -> int:
+    """Each rank tracks its own sequence (different noise and perturbations)."""
+    return base_seed + rank
+
+
+def max_over_ranks(value: float, dist=None, device="cpu") -> float:
+    """The largest of the ranks' values (the job's time is the slowest rank's)."""
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(units_per_rank: int, world: int, ms_max: float) -> float:
+    """Whole-job throughput: all ranks' units over the slowest rank's time."""
+    return units_per_rank * world / (ms_max / 1e3)
+
+
 def run_reference(args):
-    rank = int(os.environ.get("RANK", "0"))
+    world, rank, _ = world_info()
     if rank != 0:
         return 0
     steps, warm = max(1, args.steps), max(0, args.warmup)
@@ -234,14 +269,12 @@ def workload_config(args) -> dict:
 # ---------------------------------------------------------------------------
 
 def run_ours(args):
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
+    world, rank, local = world_info()
     W, K = max(3, args.warmup), max(1, args.steps)
     n_frames = 1 + W + K
     if n_frames > 300:
         raise SystemExit("--warmup + --steps must be <= 299 (300-frame trajectory)")
-    seq, depths, rels = render_frames(n_frames, args.seed + rank)
+    seq, depths, rels = render_frames(n_frames, replica_seed(args.seed, rank))
 
     import torch
     import paper_2509_24236_gb300 as pf
@@ -308,11 +341,7 @@ def run_ours(args):
     ms = t_begin.elapsed_time(t_end)
     kt = {cls: pf.pf_kernel_timing(cls) for cls in ("fitness", "fitness1", "integrate", "backproject")}
     pf.pf_set_kernel_timing(False)
-    ms_max = ms
-    if dist is not None:
-        t = torch.tensor([ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_max = float(t.item())
+    ms_max = max_over_ranks(ms, dist, dev)
 
     # per-frame statistics of the timed frames
     stats_host = stats_dev.cpu().numpy()
@@ -334,8 +363,7 @@ def run_ours(args):
     if not args.no_e2e:
         e2e = run_e2e(pf, vol, seq, depths, rels, intr, params, W, K, dev)
 
-    total_frames = K * world
-    value = total_frames / (ms_max / 1e3)
+    value = job_rate(K, world, ms_max)
     fit_ms, fit_n = kt["fitness"]
     fit_avg_ms = fit_ms / max(1, fit_n)
     samples_per_launch = samples / max(1, fit_n)
@@ -350,7 +378,7 @@ def run_ours(args):
         "fitness_vs_plain": vs_plain,
         "roofline": {"bound": "alu", "kernel": "fitness_kernel<search>", "achieved": achieved_tflops,
                      "peak": peak_tflops, "unit": "TFLOP/s", "frac": achieved_tflops / peak_tflops,
-                     "traffic": None, "avg_launch_ms": fit_avg_ms, "launches": fit_n,
+                     "traffic": committed_traffic(), "avg_launch_ms": fit_avg_ms, "launches": fit_n,
                      "flop_per_sample": FLOP_PER_SAMPLE, "samples_per_launch": samples_per_launch,
                      "peak_source": "FP32 lanes x clock: 152 SMs x 128 x 2 flop x 2070 MHz (derived)"},
         "kernel_ms": {cls: {"total_ms": v[0], "launches": v[1]} for cls, v in kt.items()},
@@ -360,7 +388,7 @@ def run_ours(args):
         "e2e": e2e,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        fps, desc, cores, times, t_int, npts = oracle_sample(seq, depths, rels, args.compose_mode, 48, repeats=1)
+        fps, desc, cores, times, t_int, npts = oracle_sample(seq, depths, rels, args.compose_mode, 1024, repeats=1)
         line["cpu_baseline"] = {"value": fps, "unit": "frames/s", "cores": cores, "kind": "oracle", "sample": desc}
     if rank == 0:
         print(json.dumps(line))
@@ -368,6 +396,25 @@ def run_ours(args):
     if dist is not None:
         dist.destroy_process_group()
     return 0
+
+
+def committed_traffic():
+    """DRAM bytes per launch of the fitness kernel from the committed ncu
+    summary, or None when csrc/track.cu has changed since that capture."""
+    import hashlib
+    import re
+    path = os.path.join(ROOT, "profiles", "fitness_kernel_multiroom.md")
+    src = os.path.join(ROOT, "paper_2509_24236_gb300", "csrc", "track.cu")
+    try:
+        text = open(path).read()
+        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    except OSError:
+        return None
+    m = re.search(r"traffic_bytes_per_launch:\s*(\d+)", text)
+    h = re.search(r"kernel_source_sha256_prefix:\s*([0-9a-f]+)", text)
+    if not m or not h or h.group(1) != sha:
+        return None
+    return int(m.group(1))
 
 
 def fp32_peak_tflops() -> float:
@@ -435,8 +482,62 @@ def run_e2e(pf, vol, seq, depths, rels, intr, params, W, K, dev):
     return {"value": K / dt, "unit": "frames/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
 
 
+def run_kernel(args):
+    """One kernel on the multiroom workload, for profiling: the volume fuses
+    frames 0 and 2 at their true poses; `fitness` evaluates 3072 poses within
+    --spread degrees / centimetres of frame 1's pose over all of frame 1's
+    points (pf_fitness, --variant); `integrate` fuses frame 1 (pf_integrate).
+    Prints one JSON line with the mean CUDA-event time per launch."""
+    import torch
+
+    import paper_2509_24236_gb300 as pf
+    import synth
+    from paper_2509_24236_gb300 import build as pfbuild
+    seq, depths, rels = render_frames(3, args.seed)
+    pfbuild.build()
+    pf.load()
+    dev = torch.device("cuda", 0)
+    intr = seq.intr
+    vol = pf.Volume.from_grid(seq.grid)
+    for f in (0, 2):
+        vol.integrate(torch.from_numpy(depths[f]).to(dev), intr, seq.gt[f])
+    depth1 = torch.from_numpy(depths[1]).to(dev)
+    if args.kernel == "fitness":
+        pts, n = pf.backproject(depth1, intr)
+        n = int(n.item())
+        pts = pts[:n].contiguous()
+        u = synth.uniform01(77, 2 * K_PARTICLES)
+        P = seq.gt[1]
+        poses = np.stack([P[:3, :4].reshape(12)] + [
+            (P @ synth.perturbation(78, k, args.spread * u[2 * k], args.spread * u[2 * k + 1]))[:3, :4].reshape(12)
+            for k in range(1, K_PARTICLES)]).astype(np.float32)
+        poses = torch.from_numpy(poses).to(dev)
+        vol.set_fitness_variant(args.variant)
+        launch = lambda: vol.fitness(pts, poses)
+        units, unit = n * K_PARTICLES, "samples"
+    else:
+        launch = lambda: vol.integrate(depth1, intr, seq.gt[1])
+        units, unit = seq.grid.n_nodes, "nodes"
+    launch()
+    torch.cuda.synchronize()
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(args.reps):
+        launch()
+    b.record()
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b) / args.reps
+    print(json.dumps({"kernel": args.kernel, "variant": args.variant, "spread": args.spread, "reps": args.reps,
+                      "ms_per_launch": ms, f"{unit}_per_s": units / (ms / 1e3)}))
+    vol.close()
+    return 0
+
+
 def main():
     args = parse()
+    if args.kernel:
+        return run_kernel(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)
