@@ -177,9 +177,12 @@ PF_API pf_status pf_pose_compose(const double* a_dev, const double* b_dev, doubl
 /* Back-project a depth image into metric camera-frame points (Sec. III,
  * problem setting): pixel (u, v) with usable depth z gives
  * ((u - cx) z / fx, (v - cy) z / fy, z).  Points of usable pixels are
- * written in row-major pixel order as float4 (x, y, z, 0) to points_dev
- * (capacity entries, >= width*height); the count is written to *n_dev
- * (device int).  No decimation (the search applies its stride itself). */
+ * written as float4 (x, y, z, 0) to points_dev (capacity entries,
+ * >= width*height) in tile order: the image is cut into 8 x 4-pixel tiles,
+ * taken row-major over tiles and row-major inside a tile (so 32 consecutive
+ * points are one compact image patch).  The count is written to *n_dev
+ * (device int).  No decimation here: the search keeps every n-th point of
+ * this order itself. */
 PF_API pf_status pf_backproject(const float* depth_dev, const pf_intrinsics* intr, float* points_dev,
                          int capacity, int* n_dev, void* cuda_stream);
 

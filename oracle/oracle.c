@@ -83,24 +83,32 @@ static int depth_valid(float z, const or_intr* in)
     return isfinite(z) && (double)z >= in->depth_min && (double)z <= in->depth_max;
 }
 
-/* Points of the valid pixels in row-major order; the j-th valid pixel is kept
- * when j mod stride == 0 (down-sampling, Sec. IV-A).  Returns the count. */
+/* Points of the valid pixels; the j-th valid pixel is kept when
+ * j mod stride == 0 (down-sampling, Sec. IV-A).  Returns the count.
+ * reading: the order of the point cloud (which decides the down-sampled
+ * subset) is tile order -- the image cut into 8 x 4-pixel tiles, taken
+ * row-major over tiles and row-major inside each tile. */
 long or_backproject(const float* depth, const or_intr* in, int stride, double* pts)
 {
     long j = 0, n = 0;
-    for (int v = 0; v < in->height; ++v)
-        for (int u = 0; u < in->width; ++u) {
-            float z = depth[(size_t)v * in->width + u];
-            if (!depth_valid(z, in)) continue;
-            if (j % stride == 0) {
-                double zd = (double)z;
-                pts[3 * n + 0] = ((double)u - in->cx) * zd / in->fx;
-                pts[3 * n + 1] = ((double)v - in->cy) * zd / in->fy;
-                pts[3 * n + 2] = zd;
-                ++n;
-            }
-            ++j;
-        }
+    int tiles_x = (in->width + 7) / 8, tiles_y = (in->height + 3) / 4;
+    for (int ty = 0; ty < tiles_y; ++ty)
+        for (int tx = 0; tx < tiles_x; ++tx)
+            for (int dv = 0; dv < 4; ++dv)
+                for (int du = 0; du < 8; ++du) {
+                    int u = tx * 8 + du, v = ty * 4 + dv;
+                    if (u >= in->width || v >= in->height) continue;
+                    float z = depth[(size_t)v * in->width + u];
+                    if (!depth_valid(z, in)) continue;
+                    if (j % stride == 0) {
+                        double zd = (double)z;
+                        pts[3 * n + 0] = ((double)u - in->cx) * zd / in->fx;
+                        pts[3 * n + 1] = ((double)v - in->cy) * zd / in->fy;
+                        pts[3 * n + 2] = zd;
+                        ++n;
+                    }
+                    ++j;
+                }
     return n;
 }
 

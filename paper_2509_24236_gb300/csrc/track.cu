@@ -54,8 +54,19 @@ struct SearchState {
 
 // ---------------------------------------------------------------------------
 // Back-projection (Sec. III, problem setting)
+//
+// Points are compacted in tile order: the image is cut into 8 x 4-pixel tiles,
+// taken row-major over tiles and row-major inside a tile, so 32 consecutive
+// points form one compact image patch -- exactly what a warp of the fitness
+// kernel evaluates together when points share the lanes, which keeps the
+// cells those 32 samples touch close together.  Down-sampling keeps every
+// n-th point of this order.  One warp per tile: a ballot gives the tile's
+// valid pixels and their ranks.
 // ---------------------------------------------------------------------------
-constexpr int BP_THREADS = 256, BP_PPT = 8, BP_CHUNK = BP_THREADS * BP_PPT;
+constexpr int TILE_W = 8, TILE_H = 4;
+constexpr int BP_THREADS = 256, BP_TILES_PER_WARP = 8;
+constexpr int BP_CHUNK_TILES = (BP_THREADS / 32) * BP_TILES_PER_WARP;  // tiles per block
+constexpr int BP_CHUNK = BP_CHUNK_TILES * 32;                         // pixel slots per block
 
 __device__ inline int block_sum_int(int v, int* sh)
 {
@@ -69,71 +80,86 @@ __device__ inline int block_sum_int(int v, int* sh)
     return tot;
 }
 
-__global__ void __launch_bounds__(BP_THREADS) bp_count_kernel(const float* __restrict__ depth, int npix,
-                                                              float dmin, float dmax, int* block_counts)
+// Pixel of `lane` in `tile`; true when it lies in the image with a usable depth.
+__device__ inline bool bp_pixel(const float* __restrict__ depth, const CamK& cam, int tiles_x, int tile, int lane,
+                                int& u, int& v, float& z)
 {
-    __shared__ int sh[32];
-    const int base = blockIdx.x * BP_CHUNK + threadIdx.x * BP_PPT;
-    int c = 0;
-#pragma unroll
-    for (int p = 0; p < BP_PPT; ++p) {
-        const int idx = base + p;
-        if (idx < npix && pf_depth_usable(depth[idx], dmin, dmax)) ++c;
-    }
-    const int tot = block_sum_int(c, sh);
-    if (threadIdx.x == 0) block_counts[blockIdx.x] = tot;
+    const int ty = tile / tiles_x, tx = tile - ty * tiles_x;
+    u = tx * TILE_W + (lane & (TILE_W - 1));
+    v = ty * TILE_H + lane / TILE_W;
+    z = 0.0f;
+    if (u >= cam.width || v >= cam.height) return false;
+    z = depth[(size_t)v * cam.width + u];
+    return pf_depth_usable(z, cam.dmin, cam.dmax);
 }
 
-__global__ void __launch_bounds__(BP_THREADS) bp_write_kernel(const float* __restrict__ depth, CamK cam,
-                                                              int npix, const int* __restrict__ block_counts,
+// Valid pixels of this warp's tiles (a warp-uniform count).
+__device__ inline int bp_warp_count(const float* __restrict__ depth, const CamK& cam, int n_tiles, int tiles_x)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int c = 0;
+    for (int i = 0; i < BP_TILES_PER_WARP; ++i) {
+        const int tile = blockIdx.x * BP_CHUNK_TILES + warp * BP_TILES_PER_WARP + i;
+        int u, v;
+        float z;
+        const bool ok = tile < n_tiles && bp_pixel(depth, cam, tiles_x, tile, lane, u, v, z);
+        c += __popc(__ballot_sync(0xffffffffu, ok));
+    }
+    return c;
+}
+
+__global__ void __launch_bounds__(BP_THREADS) bp_count_kernel(const float* __restrict__ depth, CamK cam, int n_tiles,
+                                                              int tiles_x, int* block_counts)
+{
+    __shared__ int sh[32];
+    const int c = bp_warp_count(depth, cam, n_tiles, tiles_x);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = c;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int tot = 0;
+        for (int w = 0; w < BP_THREADS / 32; ++w) tot += sh[w];
+        block_counts[blockIdx.x] = tot;
+    }
+}
+
+__global__ void __launch_bounds__(BP_THREADS) bp_write_kernel(const float* __restrict__ depth, CamK cam, int n_tiles,
+                                                              int tiles_x, const int* __restrict__ block_counts,
                                                               float4* __restrict__ pts, int* n_out)
 {
     __shared__ int sh[32];
-    __shared__ int warp_off[32];
-    // points of the earlier chunks
+    __shared__ int warp_off[BP_THREADS / 32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    // points of the earlier blocks
     int off = 0;
     for (int b = threadIdx.x; b < (int)blockIdx.x; b += blockDim.x) off += block_counts[b];
     off = block_sum_int(off, sh);
-
-    const int base = blockIdx.x * BP_CHUNK + threadIdx.x * BP_PPT;
-    float z[BP_PPT];
-    int c = 0;
-#pragma unroll
-    for (int p = 0; p < BP_PPT; ++p) {
-        const int idx = base + p;
-        z[p] = idx < npix ? depth[idx] : 0.0f;
-        if (idx < npix && pf_depth_usable(z[p], cam.dmin, cam.dmax)) ++c;
-        else z[p] = NAN;
-    }
-    // exclusive scan of c over the block, in thread order (= pixel order)
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    int incl = c;
-    for (int o = 1; o < 32; o <<= 1) {
-        int y = __shfl_up_sync(0xffffffffu, incl, o);
-        if (lane >= o) incl += y;
-    }
-    if (lane == 31) warp_off[warp] = incl;
+    // exclusive scan of the warps' counts, in warp order (= tile order)
+    const int c = bp_warp_count(depth, cam, n_tiles, tiles_x);
+    if (lane == 0) warp_off[warp] = c;
     __syncthreads();
     if (threadIdx.x == 0) {
         int acc = 0;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
-            int t = warp_off[w];
+        for (int w = 0; w < BP_THREADS / 32; ++w) {
+            const int t = warp_off[w];
             warp_off[w] = acc;
             acc += t;
         }
     }
     __syncthreads();
-    int pos = off + warp_off[warp] + incl - c;
-#pragma unroll
-    for (int p = 0; p < BP_PPT; ++p) {
-        if (z[p] == z[p]) {
-            const int idx = base + p;
-            const int v = idx / cam.width, u = idx - v * cam.width;
-            const float zz = z[p];
-            const float x = __fdiv_rn(((float)u - cam.cx) * zz, cam.fx);
-            const float y = __fdiv_rn(((float)v - cam.cy) * zz, cam.fy);
-            pts[pos++] = make_float4(x, y, zz, 0.0f);
+    int pos = off + warp_off[warp];
+    const unsigned below = (1u << lane) - 1u;
+    for (int i = 0; i < BP_TILES_PER_WARP; ++i) {
+        const int tile = blockIdx.x * BP_CHUNK_TILES + warp * BP_TILES_PER_WARP + i;
+        int u, v;
+        float z;
+        const bool ok = tile < n_tiles && bp_pixel(depth, cam, tiles_x, tile, lane, u, v, z);
+        const unsigned m = __ballot_sync(0xffffffffu, ok);
+        if (ok) {
+            const float x = __fdiv_rn(((float)u - cam.cx) * z, cam.fx);
+            const float y = __fdiv_rn(((float)v - cam.cy) * z, cam.fy);
+            pts[pos + __popc(m & below)] = make_float4(x, y, z, 0.0f);
         }
+        pos += __popc(m);
     }
     if (blockIdx.x == gridDim.x - 1 && threadIdx.x == blockDim.x - 1) *n_out = pos;
 }
@@ -141,16 +167,24 @@ __global__ void __launch_bounds__(BP_THREADS) bp_write_kernel(const float* __res
 pf_status enqueue_backproject(const float* depth, const pf_intrinsics* intr, float4* pts, int* block_counts,
                               int* n_out, cudaStream_t s)
 {
-    const int npix = intr->width * intr->height;
-    const int blocks = (npix + BP_CHUNK - 1) / BP_CHUNK;
+    const int tiles_x = (intr->width + TILE_W - 1) / TILE_W, tiles_y = (intr->height + TILE_H - 1) / TILE_H;
+    const int n_tiles = tiles_x * tiles_y;
+    const int blocks = (n_tiles + BP_CHUNK_TILES - 1) / BP_CHUNK_TILES;
     CamK cam = make_cam(intr);
     pf::timing_begin(pf::KC_BACKPROJECT, s);
-    bp_count_kernel<<<blocks, BP_THREADS, 0, s>>>(depth, npix, cam.dmin, cam.dmax, block_counts);
-    bp_write_kernel<<<blocks, BP_THREADS, 0, s>>>(depth, cam, npix, block_counts, pts, n_out);
+    bp_count_kernel<<<blocks, BP_THREADS, 0, s>>>(depth, cam, n_tiles, tiles_x, block_counts);
+    bp_write_kernel<<<blocks, BP_THREADS, 0, s>>>(depth, cam, n_tiles, tiles_x, block_counts, pts, n_out);
     pf::count_launch(2);
     pf::timing_end(pf::KC_BACKPROJECT, s);
     PF_LAUNCHED();
     return PF_OK;
+}
+
+// number of back-projection blocks for a w x h image
+int bp_blocks(int width, int height)
+{
+    const int n_tiles = ((width + TILE_W - 1) / TILE_W) * ((height + TILE_H - 1) / TILE_H);
+    return (n_tiles + BP_CHUNK_TILES - 1) / BP_CHUNK_TILES;
 }
 
 // ---------------------------------------------------------------------------
@@ -422,6 +456,19 @@ __device__ __forceinline__ void accumulate(float t, float& s, int& c)
     }
 }
 
+// Trilinear interpolation from a cell-view record: corners with their
+// x-differences already formed (v000, v100 - v000, v010, v110 - v010, ...).
+__device__ __forceinline__ float trilerp_cell(float fx, float fy, float fz, float4 lo, float4 hi)
+{
+    const float x00 = fmaf(fx, lo.y, lo.x);
+    const float x10 = fmaf(fx, lo.w, lo.z);
+    const float x01 = fmaf(fx, hi.y, hi.x);
+    const float x11 = fmaf(fx, hi.w, hi.z);
+    const float y0 = fmaf(fy, x10 - x00, x00);
+    const float y1 = fmaf(fy, x11 - x01, x01);
+    return fmaf(fz, y1 - y0, y0);
+}
+
 __device__ __forceinline__ float trilerp(float fx, float fy, float fz, float v000, float v100, float v010, float v110,
                                          float v001, float v101, float v011, float v111)
 {
@@ -438,17 +485,29 @@ __device__ __forceinline__ float trilerp(float fx, float fy, float fz, float v00
 // interpolated value non-finite, so validity is one comparison on the
 // result); 1: plain tsdf + weight, all eight nodes tested explicitly;
 // 2: the cell view, whose eight corners are one 32-byte sector.
-template <int VARIANT>
+// BRANCHLESS (cell view only): a sample outside the grid reads cell 0 and is
+// dropped by the final predicate instead of a branch -- cheaper when almost
+// every sample lands inside, as when particles share the lanes of a warp.
+template <int VARIANT, bool BRANCHLESS = false>
 __device__ __forceinline__ void sample(const FitArgs& a, int nx, int nxy, unsigned mx, unsigned my, unsigned mz,
                                        const Xform& X, float x, float y, float z, const int* Yi, const float* Yf,
                                        float& s, int& c)
 {
     const Cell q = locate(X, nx, nxy, mx, my, mz, x, y, z, Yi, Yf);
+    if (VARIANT == 2 && BRANCHLESS) {
+        const float4* p = a.cells + 2 * (size_t)(q.ok ? q.idx : 0);
+        const float4 lo = __ldg(p), hi = __ldg(p + 1);
+        const float t = fabsf(trilerp_cell(q.fx, q.fy, q.fz, lo, hi));
+        const bool use = q.ok && t < INFINITY;
+        s += use ? t : 0.0f;
+        c += use ? 1 : 0;
+        return;
+    }
     if (!q.ok) return;
     if (VARIANT == 2) {
         const float4* p = a.cells + 2 * (size_t)q.idx;
         const float4 lo = __ldg(p), hi = __ldg(p + 1);
-        accumulate(trilerp(q.fx, q.fy, q.fz, lo.x, lo.y, lo.z, lo.w, hi.x, hi.y, hi.z, hi.w), s, c);
+        accumulate(trilerp_cell(q.fx, q.fy, q.fz, lo, hi), s, c);
     } else if (VARIANT == 0) {
         const float* p = a.tsdf + q.idx;
         accumulate(trilerp(q.fx, q.fy, q.fz, __ldg(p), __ldg(p + 1), __ldg(p + nx), __ldg(p + nx + 1), __ldg(p + nxy),
@@ -646,7 +705,7 @@ __global__ void __launch_bounds__(FIT_THREADS, PF_FIT_MIN_BLOCKS) fitness_kernel
                     const float4 yp = sPts[warp][q][1];
                     const int yi[3] = {__float_as_int(xp.w), __float_as_int(yp.w), sYz[warp][q]};
                     const float yf[3] = {yp.x, yp.y, yp.z};
-                    sample<VARIANT>(a, nx, nxy, mx, my, mz, X, xp.x, xp.y, xp.z, yi, yf, s, c);
+                    sample<VARIANT, true>(a, nx, nxy, mx, my, mz, X, xp.x, xp.y, xp.z, yi, yf, s, c);
                 }
                 __syncwarp();
                 if (lane < kc) {
@@ -993,7 +1052,9 @@ pf_status workspace_reserve(pf_volume* v, int max_pixels, int k_max)
         w.block_counts = nullptr;
         w.pix_cap = 0;
         PF_CUDA(cudaMalloc(&w.points, sizeof(float4) * (size_t)max_pixels));
-        PF_CUDA(cudaMalloc(&w.block_counts, sizeof(int) * ((size_t)max_pixels / BP_CHUNK + 2)));
+        // one count per back-projection block: an image of max_pixels pixels has
+        // at most max_pixels tiles (thin images leave tiles partly empty)
+        PF_CUDA(cudaMalloc(&w.block_counts, sizeof(int) * ((size_t)max_pixels / BP_CHUNK_TILES + 2)));
         w.pix_cap = max_pixels;
     }
     if (!w.state) {
@@ -1021,7 +1082,7 @@ pf_status pf_backproject(const float* depth_dev, const pf_intrinsics* intr, floa
     const long long npix = (long long)intr->width * intr->height;
     if (capacity < npix) return PF_ERR_INVALID_ARG;
     int* counts = nullptr;
-    const int blocks = (int)((npix + BP_CHUNK - 1) / BP_CHUNK);
+    const int blocks = bp_blocks(intr->width, intr->height);
     PF_CUDA(cudaMallocAsync(&counts, sizeof(int) * blocks, (cudaStream_t)stream));
     st = enqueue_backproject(depth_dev, intr, reinterpret_cast<float4*>(points_dev), counts, n_dev,
                              (cudaStream_t)stream);

@@ -136,10 +136,14 @@ __global__ void fill_kernel(float* tsdf, float* weight, size_t n)
 }
 
 // Cell view: for every cell (lower corner node i, j, k) its eight encoded
-// corner values, x fastest: float4 (v000 v100 v010 v110), float4 (v001 v101
-// v011 v111).  A cell depends on the nodes of its own fusion tile and of the
-// next tiles along +x, +y, +z, so a tile is rewritten when any of those was
-// reached by the last fusion (or always, after a reset or upload).
+// corner values with the x-differences the interpolation needs already
+// formed: float4 (v000, v100 - v000, v010, v110 - v010) and float4 (v001,
+// v101 - v001, v011, v111 - v011).  The subtraction is the same float
+// operation the fitness would do, so results are bit-identical, and a
+// non-finite corner still makes the interpolated value non-finite.  A cell
+// depends on the nodes of its own fusion tile and of the next tiles along
+// +x, +y, +z, so a tile is rewritten when any of those was reached by the
+// last fusion (or always, after a reset or upload).
 struct RefreshArgs {
     const float* tsdf;
     float4* cells;
@@ -171,8 +175,10 @@ __global__ void __launch_bounds__(TX * TY, 4) cells_refresh_kernel(RefreshArgs a
         if (k >= a.nz - 1) break;
         const size_t idx = i + nx * j + nxy * k;
         const float* p = a.tsdf + idx;
-        const float4 lo = make_float4(p[0], p[1], p[nx], p[nx + 1]);
-        const float4 hi = make_float4(p[nxy], p[nxy + 1], p[nxy + nx], p[nxy + nx + 1]);
+        const float v000 = p[0], v100 = p[1], v010 = p[nx], v110 = p[nx + 1];
+        const float v001 = p[nxy], v101 = p[nxy + 1], v011 = p[nxy + nx], v111 = p[nxy + nx + 1];
+        const float4 lo = make_float4(v000, v100 - v000, v010, v110 - v010);
+        const float4 hi = make_float4(v001, v101 - v001, v011, v111 - v011);
         a.cells[2 * idx] = lo;
         a.cells[2 * idx + 1] = hi;
     }

@@ -69,6 +69,26 @@ def test_backprojected_points_lie_on_the_analytic_surface():
     assert np.max(np.abs(scene.sdf(Xw))) < 5e-6
 
 
+def test_backprojection_tile_order():
+    """Points follow 8 x 4-pixel tiles, row-major over tiles and inside each."""
+    W, H = 19, 10
+    intr = Intrinsics(W, H, 10.0, 10.0, 9.0, 4.5, 0.5, 3.0)
+    d = (1.0 + np.arange(W * H, dtype=np.float32) / 1000.0).reshape(H, W)   # depth encodes the pixel
+    d[3, 7] = 0.0
+    pts = _orc().backproject(d, intr, 1)
+    order = []
+    for ty in range(0, H, 4):
+        for tx in range(0, W, 8):
+            for v in range(ty, min(ty + 4, H)):
+                for u in range(tx, min(tx + 8, W)):
+                    if d[v, u] > 0:
+                        order.append((v, u))
+    assert pts.shape[0] == len(order) == W * H - 1
+    assert np.array_equal(pts[:, 2], np.array([d[v, u] for v, u in order], dtype=np.float64))
+    for s in (3, 8):
+        assert np.array_equal(_orc().backproject(d, intr, s), pts[::s])
+
+
 def test_backprojection_validity_order_and_stride():
     intr = Intrinsics(5, 4, 10.0, 10.0, 2.0, 1.5, 0.5, 3.0)
     d = np.full((4, 5), 1.0, dtype=np.float32)
@@ -80,6 +100,7 @@ def test_backprojection_validity_order_and_stride():
     d[2, 2] = 3.0       # exactly depth_max: usable
     d[0, 0] = 0.5       # exactly depth_min: usable
     full = _orc().backproject(d, intr, 1)
+    # a 5 x 4 image is a single 8 x 4 tile: tile order is row-major here
     valid = [(v, u) for v in range(4) for u in range(5)
              if np.isfinite(d[v, u]) and 0.5 <= d[v, u] <= 3.0]
     assert full.shape[0] == len(valid) == 15
