@@ -53,6 +53,9 @@ def parse():
     ap.add_argument("--update-mode", type=int, default=0)
     ap.add_argument("--compose-mode", type=int, default=1)
     ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--tsdf-dtype", default="f32", choices=["f32", "f16", "bf16"],
+                    help="storage type of the TSDF and its cell view (arithmetic stays f32)")
+    ap.add_argument("--weight-u8", action="store_true", help="store fusion weights as uint8")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ref-particles", type=int, default=192,
@@ -250,9 +253,18 @@ def run_reference(args):
     return 0
 
 
+def storage_desc(args) -> str:
+    return f"{args.tsdf_dtype} tsdf + {'u8' if args.weight_u8 else 'f32'} weight"
+
+
+def new_volume(pf, grid, args):
+    dt = {"f32": pf.PF_F32, "f16": pf.PF_F16, "bf16": pf.PF_BF16}[args.tsdf_dtype]
+    return pf.Volume.from_grid(grid, tsdf_dtype=dt, weight_u8=int(args.weight_u8))
+
+
 def workload_config(args) -> dict:
     return {
-        "workload": "multiroom: 640x480 depth, 512^3 TSDF @ 1 cm (tau 3 cm, f32 tsdf + f32 weight), "
+        "workload": f"multiroom: 640x480 depth, 512^3 TSDF @ 1 cm (tau 3 cm, {storage_desc(args)}), "
                     "3072 particles x 20 iterations over all points, then fusion",
         "resolution": "640x480", "volume": "512^3", "voxel_m": 0.01, "trunc_m": 0.03,
         "particles": K_PARTICLES, "iterations": N_ITERS, "decimation": 1,
@@ -261,6 +273,7 @@ def workload_config(args) -> dict:
         "init_perturbation": "3 deg / 3 cm", "seed": args.seed,
         "l2": "inputs larger than L2: fusion reads and writes the 1.07 GB volume frustum every step",
         "parallelism": f"replicas x{args.gpus}",
+        "storage": storage_desc(args),
     }
 
 
@@ -294,7 +307,7 @@ def run_ours(args):
 
     intr, grid = seq.intr, seq.grid
     stream = torch.cuda.current_stream()
-    vol = pf.Volume.from_grid(grid)
+    vol = new_volume(pf, grid, args)
     vol.set_fitness_variant(args.variant)
     vol.reserve(intr.width * intr.height, K_PARTICLES)
     import synth
@@ -356,7 +369,9 @@ def run_ours(args):
     ate_cm = 100.0 * float(np.sqrt(np.mean(np.square(err))))
 
     # ---- fitness kernel throughput, encoded vs plain layout --------------
-    vs_plain = fitness_vs_plain(pf, vol, depth_dev[W + 1], intr, poses[W], dev)
+    # (the plain layout exists for float storage only)
+    vs_plain = fitness_vs_plain(pf, vol, depth_dev[W + 1], intr, poses[W], dev) if args.tsdf_dtype == "f32" \
+        and not args.weight_u8 else None
 
     # ---- end-to-end pass through the host API ----------------------------
     e2e = None
@@ -498,7 +513,7 @@ def run_kernel(args):
     pf.load()
     dev = torch.device("cuda", 0)
     intr = seq.intr
-    vol = pf.Volume.from_grid(seq.grid)
+    vol = new_volume(pf, seq.grid, args)
     for f in (0, 2):
         vol.integrate(torch.from_numpy(depths[f]).to(dev), intr, seq.gt[f])
     depth1 = torch.from_numpy(depths[1]).to(dev)
@@ -529,6 +544,7 @@ def run_kernel(args):
     torch.cuda.synchronize()
     ms = a.elapsed_time(b) / args.reps
     print(json.dumps({"kernel": args.kernel, "variant": args.variant, "spread": args.spread, "reps": args.reps,
+                      "storage": storage_desc(args),
                       "ms_per_launch": ms, f"{unit}_per_s": units / (ms / 1e3)}))
     vol.close()
     return 0

@@ -62,16 +62,22 @@ typedef struct {
     float depth_min, depth_max;
 } pf_intrinsics;
 
-/* Storage type of the TSDF values.  This version stores PF_F32 only; other
- * values are rejected with PF_ERR_UNSUPPORTED. */
+/* Storage type of the TSDF values (and of the cell view).  PF_F32, PF_F16
+ * and PF_BF16 are supported; PF_FP8E4M3 is rejected with PF_ERR_UNSUPPORTED.
+ * A 16-bit grid stores the value rounded to nearest; a value that rounds to
+ * +-1 is stored as the outside-the-band code (+-1 exactly), so the fitness
+ * treats such a node as outside the band.  All arithmetic (fusion average,
+ * trilinear sample, sums) is float; only the stored values are rounded. */
 typedef enum { PF_F32 = 0, PF_F16 = 1, PF_BF16 = 2, PF_FP8E4M3 = 3 } pf_dtype;
 
 /* Dense TSDF grid (Sec. III: "a tensor that records the distance value in
  * each 3D grid").  nx, ny, nz in [2, 4096] with nx*ny*nz < 2^31;
  * voxel_size > 0; trunc (tau, metres) > 0; max_weight in [1, 65535] caps the
- * running-average weight; weight_u8 must be 0 in this version.
+ * running-average weight; weight_u8 = 1 stores weights as uint8 (then
+ * max_weight <= 255), 0 as float.
  * cell_view: the fitness reads a second copy of the grid in which the eight
- * corner values of every cell are contiguous (32 bytes per node, kept up to
+ * corner values of every cell are contiguous (32 bytes per node, 16 for a
+ * 16-bit grid, kept up to
  * date by fusion); 0 = when it needs at most 16 GiB, 1 = always, -1 = never. */
 typedef struct {
     int nx, ny, nz;

@@ -323,15 +323,16 @@ class Volume:
     """A TSDF volume on the current CUDA device (owns pf_volume)."""
 
     def __init__(self, nx, ny, nz, voxel_size, trunc, origin=(0.0, 0.0, 0.0), max_weight=255, cell_view=0,
-                 stream=None):
-        self.desc = pf_volume_desc(nx, ny, nz, voxel_size, trunc, (C.c_float * 3)(*origin), PF_F32, 0, max_weight,
-                                   cell_view)
+                 stream=None, tsdf_dtype=PF_F32, weight_u8=0):
+        self.desc = pf_volume_desc(nx, ny, nz, voxel_size, trunc, (C.c_float * 3)(*origin), tsdf_dtype, weight_u8,
+                                   max_weight, cell_view)
         self.n_nodes = nx * ny * nz
         self.handle = pf_create_volume(self.desc, stream)
 
     @classmethod
-    def from_grid(cls, grid, max_weight=255, cell_view=0):
-        return cls(grid.nx, grid.ny, grid.nz, grid.voxel_size, grid.trunc, grid.origin, max_weight, cell_view)
+    def from_grid(cls, grid, max_weight=255, cell_view=0, tsdf_dtype=PF_F32, weight_u8=0):
+        return cls(grid.nx, grid.ny, grid.nz, grid.voxel_size, grid.trunc, grid.origin, max_weight, cell_view,
+                   tsdf_dtype=tsdf_dtype, weight_u8=weight_u8)
 
     def close(self):
         if getattr(self, "handle", None):

@@ -1,6 +1,8 @@
 // Internal declarations shared by the translation units of libprofusion.
 #pragma once
 
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -46,6 +48,34 @@ __host__ __device__ inline float pf_decode(float e)
 }
 
 // --------------------------------------------------------------------------
+// Storage types.  The tsdf (and the cell view) are stored as float, half or
+// bfloat16 -- the encoding above survives the conversion (NaN and infinities
+// are kept) and a value that rounds to +-1 is stored as +-infinity, so a
+// finite stored value always lies inside the band -- and the weight as float
+// or uint8.  All arithmetic is float.
+// --------------------------------------------------------------------------
+__host__ __device__ inline float pf_to_float(float v) { return v; }
+__host__ __device__ inline float pf_to_float(__half v) { return __half2float(v); }
+__host__ __device__ inline float pf_to_float(__nv_bfloat16 v) { return __bfloat162float(v); }
+__host__ __device__ inline float pf_to_float(uint8_t v) { return (float)v; }
+
+template <typename T> __host__ __device__ inline T pf_from_float(float v);
+template <> __host__ __device__ inline float pf_from_float<float>(float v) { return v; }
+template <> __host__ __device__ inline __half pf_from_float<__half>(float v)
+{
+    const float r = __half2float(__float2half_rn(v));
+    return __float2half_rn(r >= 1.0f ? INFINITY : (r <= -1.0f ? -INFINITY : v));
+}
+template <> __host__ __device__ inline __nv_bfloat16 pf_from_float<__nv_bfloat16>(float v)
+{
+    const float r = __bfloat162float(__float2bfloat16_rn(v));
+    return __float2bfloat16_rn(r >= 1.0f ? INFINITY : (r <= -1.0f ? -INFINITY : v));
+}
+template <> __host__ __device__ inline uint8_t pf_from_float<uint8_t>(float v) { return (uint8_t)v; }
+
+inline size_t pf_dtype_size(pf_dtype t) { return t == PF_F32 ? 4 : 2; }
+
+// --------------------------------------------------------------------------
 // Volume and workspace
 // --------------------------------------------------------------------------
 struct pf_workspace {
@@ -72,9 +102,9 @@ struct pf_volume {
     pf_volume_desc desc;
     int device = 0;
     size_t n_nodes = 0;
-    float* tsdf = nullptr;     // encoded, see above
-    float* weight = nullptr;
-    float4* cells = nullptr;   // cell view: 2 float4 per node (the cell whose lower corner it is)
+    void* tsdf = nullptr;      // encoded, see above; float, half or bfloat16 (desc.tsdf_dtype)
+    void* weight = nullptr;    // float, or uint8 when desc.weight_u8
+    void* cells = nullptr;     // cell view: 8 values per node (the cell whose lower corner it is)
     int* tile_stamp = nullptr; // per fusion tile: stamp of the last fusion that reached it
     int stamp = 0;             // fusions so far
     int tiles[3] = {0, 0, 0};

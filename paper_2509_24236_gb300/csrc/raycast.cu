@@ -11,8 +11,8 @@
 namespace {
 
 struct RayArgs {
-    const float* tsdf;
-    const float* weight;
+    const void* tsdf;
+    const void* weight;
     int nx, ny, nz;
     float inv_vs;
     float org[3];
@@ -27,6 +27,7 @@ struct RayArgs {
 
 // Trilinear value of an observed cell at world point q; false when the cell
 // is outside the grid or has an unobserved node.
+template <typename TS>
 __device__ inline bool sample_observed(const RayArgs& a, float qx, float qy, float qz, float& out)
 {
     const float gx = (qx - a.org[0]) * a.inv_vs;
@@ -42,7 +43,7 @@ __device__ inline bool sample_observed(const RayArgs& a, float qx, float qy, flo
     float v[8];
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
-        const float e = __ldg(a.tsdf + base + off[q]);
+        const float e = pf_to_float(static_cast<const TS*>(a.tsdf)[base + off[q]]);
         if (e != e) return false;  // unobserved
         v[q] = pf_decode(e);
     }
@@ -57,6 +58,7 @@ __device__ inline bool sample_observed(const RayArgs& a, float qx, float qy, flo
     return true;
 }
 
+template <typename TS>
 __global__ void raycast_kernel(RayArgs a)
 {
     const int u = blockIdx.x * blockDim.x + threadIdx.x;
@@ -73,7 +75,7 @@ __global__ void raycast_kernel(RayArgs a)
     for (int i = 0; i <= a.nsteps; ++i) {
         const float z = fmaf((float)i, a.step, a.cam.dmin);
         float t;
-        if (!sample_observed(a, fmaf(z, dx, a.t[0]), fmaf(z, dy, a.t[1]), fmaf(z, dz, a.t[2]), t)) {
+        if (!sample_observed<TS>(a, fmaf(z, dx, a.t[0]), fmaf(z, dy, a.t[1]), fmaf(z, dz, a.t[2]), t)) {
             have_prev = false;
             continue;
         }
@@ -97,7 +99,7 @@ __global__ void raycast_kernel(RayArgs a)
                 qp[ax] += a.half_vs;
                 qm[ax] -= a.half_vs;
                 float tp, tm;
-                ok = sample_observed(a, qp[0], qp[1], qp[2], tp) && sample_observed(a, qm[0], qm[1], qm[2], tm);
+                ok = sample_observed<TS>(a, qp[0], qp[1], qp[2], tp) && sample_observed<TS>(a, qm[0], qm[1], qm[2], tm);
                 g[ax] = tp - tm;
             }
             if (ok) {
@@ -142,7 +144,12 @@ extern "C" pf_status pf_raycast(const pf_volume* v, const pf_intrinsics* intr, c
     dim3 grid((intr->width + 15) / 16, (intr->height + 7) / 8);
     cudaStream_t s = (cudaStream_t)stream;
     pf::timing_begin(pf::KC_RAYCAST, s);
-    raycast_kernel<<<grid, block, 0, s>>>(a);
+    if (v->desc.tsdf_dtype == PF_F16)
+        raycast_kernel<__half><<<grid, block, 0, s>>>(a);
+    else if (v->desc.tsdf_dtype == PF_BF16)
+        raycast_kernel<__nv_bfloat16><<<grid, block, 0, s>>>(a);
+    else
+        raycast_kernel<float><<<grid, block, 0, s>>>(a);
     pf::count_launch();
     pf::timing_end(pf::KC_RAYCAST, s);
     PF_LAUNCHED();

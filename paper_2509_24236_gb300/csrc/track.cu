@@ -212,9 +212,9 @@ struct FitArgs {
     double beta;
     float min_valid_frac;
     // volume
-    const float* tsdf;
-    const float* weight;
-    const float4* cells;
+    const void* tsdf;
+    const void* weight;
+    const void* cells;
     int nx, ny, nz;
     double vs;
     double org[3];
@@ -481,22 +481,59 @@ __device__ __forceinline__ float trilerp(float fx, float fy, float fz, float v00
     return fmaf(fz, y1 - y0, y0);
 }
 
+// A cell-view record as two float4: (v000, v100 - v000, v010, v110 - v010)
+// and (v001, v101 - v001, v011, v111 - v011).  Float storage keeps that form
+// (two 16-byte loads of one sector); half / bfloat16 storage keeps the eight
+// corners as stored (one 16-byte load) and the differences are formed here.
+__device__ __forceinline__ void load_cell(const float* cells, int idx, float4& lo, float4& hi)
+{
+    const float4* p = reinterpret_cast<const float4*>(cells) + 2 * (size_t)idx;
+    lo = __ldg(p);
+    hi = __ldg(p + 1);
+}
+
+__device__ __forceinline__ void corners_to_cell(float v000, float v100, float v010, float v110, float v001,
+                                                float v101, float v011, float v111, float4& lo, float4& hi)
+{
+    lo = make_float4(v000, v100 - v000, v010, v110 - v010);
+    hi = make_float4(v001, v101 - v001, v011, v111 - v011);
+}
+
+__device__ __forceinline__ void load_cell(const __half* cells, int idx, float4& lo, float4& hi)
+{
+    const uint4 r = __ldg(reinterpret_cast<const uint4*>(cells) + idx);
+    const float2 a = __half22float2(*reinterpret_cast<const __half2*>(&r.x));
+    const float2 b = __half22float2(*reinterpret_cast<const __half2*>(&r.y));
+    const float2 c = __half22float2(*reinterpret_cast<const __half2*>(&r.z));
+    const float2 d = __half22float2(*reinterpret_cast<const __half2*>(&r.w));
+    corners_to_cell(a.x, a.y, b.x, b.y, c.x, c.y, d.x, d.y, lo, hi);
+}
+
+__device__ __forceinline__ void load_cell(const __nv_bfloat16* cells, int idx, float4& lo, float4& hi)
+{
+    // a bfloat16 is the upper half of a float
+    const uint4 r = __ldg(reinterpret_cast<const uint4*>(cells) + idx);
+    corners_to_cell(__uint_as_float(r.x << 16), __uint_as_float(r.x & 0xffff0000u), __uint_as_float(r.y << 16),
+                    __uint_as_float(r.y & 0xffff0000u), __uint_as_float(r.z << 16), __uint_as_float(r.z & 0xffff0000u),
+                    __uint_as_float(r.w << 16), __uint_as_float(r.w & 0xffff0000u), lo, hi);
+}
+
 // One sample.  VARIANT 0: encoded tsdf nodes (non-finite nodes make the
 // interpolated value non-finite, so validity is one comparison on the
-// result); 1: plain tsdf + weight, all eight nodes tested explicitly;
-// 2: the cell view, whose eight corners are one 32-byte sector.
+// result); 1: plain tsdf + weight (float), all eight nodes tested
+// explicitly; 2: the cell view.  TS is the storage type of tsdf and cells.
 // BRANCHLESS (cell view only): a sample outside the grid reads cell 0 and is
 // dropped by the final predicate instead of a branch -- cheaper when almost
 // every sample lands inside, as when particles share the lanes of a warp.
-template <int VARIANT, bool BRANCHLESS = false>
+template <int VARIANT, typename TS, bool BRANCHLESS = false>
 __device__ __forceinline__ void sample(const FitArgs& a, int nx, int nxy, unsigned mx, unsigned my, unsigned mz,
                                        const Xform& X, float x, float y, float z, const int* Yi, const float* Yf,
                                        float& s, int& c)
 {
     const Cell q = locate(X, nx, nxy, mx, my, mz, x, y, z, Yi, Yf);
     if (VARIANT == 2 && BRANCHLESS) {
-        const float4* p = a.cells + 2 * (size_t)(q.ok ? q.idx : 0);
-        const float4 lo = __ldg(p), hi = __ldg(p + 1);
+        float4 lo, hi;
+        load_cell(static_cast<const TS*>(a.cells), q.ok ? q.idx : 0, lo, hi);
         const float t = fabsf(trilerp_cell(q.fx, q.fy, q.fz, lo, hi));
         const bool use = q.ok && t < INFINITY;
         s += use ? t : 0.0f;
@@ -505,22 +542,25 @@ __device__ __forceinline__ void sample(const FitArgs& a, int nx, int nxy, unsign
     }
     if (!q.ok) return;
     if (VARIANT == 2) {
-        const float4* p = a.cells + 2 * (size_t)q.idx;
-        const float4 lo = __ldg(p), hi = __ldg(p + 1);
+        float4 lo, hi;
+        load_cell(static_cast<const TS*>(a.cells), q.idx, lo, hi);
         accumulate(trilerp_cell(q.fx, q.fy, q.fz, lo, hi), s, c);
     } else if (VARIANT == 0) {
-        const float* p = a.tsdf + q.idx;
-        accumulate(trilerp(q.fx, q.fy, q.fz, __ldg(p), __ldg(p + 1), __ldg(p + nx), __ldg(p + nx + 1), __ldg(p + nxy),
-                           __ldg(p + nxy + 1), __ldg(p + nxy + nx), __ldg(p + nxy + nx + 1)),
+        const TS* p = static_cast<const TS*>(a.tsdf) + q.idx;
+        accumulate(trilerp(q.fx, q.fy, q.fz, pf_to_float(p[0]), pf_to_float(p[1]), pf_to_float(p[nx]),
+                           pf_to_float(p[nx + 1]), pf_to_float(p[nxy]), pf_to_float(p[nxy + 1]),
+                           pf_to_float(p[nxy + nx]), pf_to_float(p[nxy + nx + 1])),
                    s, c);
     } else {
+        const float* tsdf = static_cast<const float*>(a.tsdf);
+        const float* weight = static_cast<const float*>(a.weight);
         const int off[8] = {0, 1, nx, nx + 1, nxy, nxy + 1, nxy + nx, nxy + nx + 1};
         float v[8];
         bool ok = true;
 #pragma unroll
         for (int r = 0; r < 8; ++r) {
-            const float w = __ldg(a.weight + q.idx + off[r]);
-            v[r] = __ldg(a.tsdf + q.idx + off[r]);
+            const float w = __ldg(weight + q.idx + off[r]);
+            v[r] = __ldg(tsdf + q.idx + off[r]);
             ok = ok && (w > 0.0f) && (fabsf(v[r]) < 1.0f);
         }
         if (ok) {
@@ -564,7 +604,7 @@ __device__ inline void argmin_pair(float& e, int& k, float* se, int* sk)
 #define PF_FIT_MIN_BLOCKS 3
 #endif
 
-template <int SRC, int VARIANT>
+template <int SRC, int VARIANT, typename TS>
 __global__ void __launch_bounds__(FIT_THREADS, PF_FIT_MIN_BLOCKS) fitness_kernel(FitArgs a)
 {
     __shared__ Particle sP[KC];
@@ -676,7 +716,7 @@ __global__ void __launch_bounds__(FIT_THREADS, PF_FIT_MIN_BLOCKS) fitness_kernel
                     int c = 0;
 #pragma unroll
                     for (int p = 0; p < PPT; ++p)
-                        sample<VARIANT>(a, nx, nxy, mx, my, mz, X, px[p], py[p], pz[p], Yi[p], Yf[p], s, c);
+                        sample<VARIANT, TS>(a, nx, nxy, mx, my, mz, X, px[p], py[p], pz[p], Yi[p], Yf[p], s, c);
 #pragma unroll
                     for (int o = 16; o > 0; o >>= 1) {
                         s += __shfl_xor_sync(0xffffffffu, s, o);
@@ -705,7 +745,7 @@ __global__ void __launch_bounds__(FIT_THREADS, PF_FIT_MIN_BLOCKS) fitness_kernel
                     const float4 yp = sPts[warp][q][1];
                     const int yi[3] = {__float_as_int(xp.w), __float_as_int(yp.w), sYz[warp][q]};
                     const float yf[3] = {yp.x, yp.y, yp.z};
-                    sample<VARIANT, true>(a, nx, nxy, mx, my, mz, X, xp.x, xp.y, xp.z, yi, yf, s, c);
+                    sample<VARIANT, TS, true>(a, nx, nxy, mx, my, mz, X, xp.x, xp.y, xp.z, yi, yf, s, c);
                 }
                 __syncwarp();
                 if (lane < kc) {
@@ -955,21 +995,32 @@ int choose_ptiles(int dev, int chunks, long long ne_max)
 constexpr float kParticleLanesBelowCells = 5.0f;
 constexpr float kParticleLanesBelowNodes = 12.0f;
 
+template <int SRC, typename TS>
+void launch_fitness_t(const FitArgs& a, int layout, dim3 grid, cudaStream_t s)
+{
+    if (layout == 2)
+        fitness_kernel<SRC, 0, TS><<<grid, FIT_THREADS, 0, s>>>(a);
+    else
+        fitness_kernel<SRC, 2, TS><<<grid, FIT_THREADS, 0, s>>>(a);
+}
+
 template <int SRC>
-void launch_fitness(FitArgs a, int variant, bool has_cells, int chunks, cudaStream_t s)
+void launch_fitness(FitArgs a, int variant, const pf_volume* v, int chunks, cudaStream_t s)
 {
     const int mapping = (variant >> 2) & 3;
     int layout = variant & 3;
-    if (layout == 0) layout = has_cells ? 3 : 2;
+    if (layout == 0) layout = v->cells ? 3 : 2;
     const float auto_threshold = layout == 3 ? kParticleLanesBelowCells : kParticleLanesBelowNodes;
     a.pm_threshold = mapping == 1 ? -1.0f : mapping == 2 ? INFINITY : auto_threshold;
     dim3 grid(chunks, a.n_ptiles);
-    if (layout == 2)
-        fitness_kernel<SRC, 0><<<grid, FIT_THREADS, 0, s>>>(a);
-    else if (layout == 1)
-        fitness_kernel<SRC, 1><<<grid, FIT_THREADS, 0, s>>>(a);
+    if (layout == 1)  // the plain baseline: float tsdf and weights
+        fitness_kernel<SRC, 1, float><<<grid, FIT_THREADS, 0, s>>>(a);
+    else if (v->desc.tsdf_dtype == PF_F16)
+        launch_fitness_t<SRC, __half>(a, layout, grid, s);
+    else if (v->desc.tsdf_dtype == PF_BF16)
+        launch_fitness_t<SRC, __nv_bfloat16>(a, layout, grid, s);
     else
-        fitness_kernel<SRC, 2><<<grid, FIT_THREADS, 0, s>>>(a);
+        launch_fitness_t<SRC, float>(a, layout, grid, s);
     pf::count_launch();
 }
 
@@ -1117,7 +1168,7 @@ pf_status pf_fitness(const pf_volume* cv, const float* points_dev, int n, const 
     a.out_C = count_dev;
     cudaStream_t s = (cudaStream_t)stream;
     pf::timing_begin(pf::KC_FITNESS, s);
-    launch_fitness<SRC_POSES>(a, v->fitness_variant, v->cells != nullptr, chunks, s);
+    launch_fitness<SRC_POSES>(a, v->fitness_variant, v, chunks, s);
     pf::timing_end(pf::KC_FITNESS, s);
     PF_LAUNCHED();
     return PF_OK;
@@ -1178,14 +1229,14 @@ pf_status pf_track_frame_async(pf_volume* v, const float* depth_dev, const pf_in
         a.n_ptiles = choose_ptiles(v->device, chunks, ne_max);
         if ((size_t)a.n_ptiles * K > (size_t)w.part_cap) return PF_ERR_INVALID_ARG;
         pf::timing_begin(pf::KC_FITNESS, s);
-        launch_fitness<SRC_SEARCH>(a, v->fitness_variant, v->cells != nullptr, chunks, s);
+        launch_fitness<SRC_SEARCH>(a, v->fitness_variant, v, chunks, s);
         pf::timing_end(pf::KC_FITNESS, s);
         if (p->update_mode == 0) {
             FitArgs e = a;
             e.K = 1;
             e.n_ptiles = choose_ptiles(v->device, 1, ne_max);
             pf::timing_begin(pf::KC_FITNESS1, s);
-            launch_fitness<SRC_EVAL>(e, v->fitness_variant, v->cells != nullptr, 1, s);
+            launch_fitness<SRC_EVAL>(e, v->fitness_variant, v, 1, s);
             pf::timing_end(pf::KC_FITNESS1, s);
         }
     }
@@ -1305,7 +1356,7 @@ extern "C" pf_status pf_fitness_noalloc(const pf_volume* v, const float* points_
     cudaStream_t s = (cudaStream_t)stream;
     // the array keeps the previous call's contents: the counter must start at zero
     PF_CUDA(cudaMemsetAsync(&sc->counter, 0, sizeof(unsigned int), s));
-    launch_fitness<SRC_POSES>(a, v->fitness_variant, v->cells != nullptr, chunks, s);
+    launch_fitness<SRC_POSES>(a, v->fitness_variant, v, chunks, s);
     PF_LAUNCHED();
     return PF_OK;
 }

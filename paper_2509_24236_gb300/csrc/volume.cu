@@ -18,6 +18,7 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <cstring>
 #include <vector>
 
 #include "pf_internal.cuh"
@@ -27,8 +28,8 @@ namespace {
 constexpr int TX = PF_TX, TY = PF_TY, TZ = PF_TZ;
 
 struct IntegArgs {
-    float* tsdf;
-    float* weight;
+    void* tsdf;
+    void* weight;
     int nx, ny, nz;
     float trunc;
     float max_weight;
@@ -45,8 +46,11 @@ struct IntegArgs {
     int stamp;
 };
 
+template <typename TS, typename TW>
 __global__ void __launch_bounds__(TX * TY, 4) integrate_kernel(IntegArgs a)
 {
+    TS* const tsdf = static_cast<TS*>(a.tsdf);
+    TW* const weight = static_cast<TW*>(a.weight);
     __shared__ float s_base[4];
     __shared__ float s_step[9];
     __shared__ int s_skip;
@@ -116,22 +120,25 @@ __global__ void __launch_bounds__(TX * TY, 4) integrate_kernel(IntegArgs a)
         const float sdf = (d - bz_hi) - zl;
         if (sdf < -a.trunc) continue;
         const float t = fminf(1.0f, __fdiv_rn(sdf, a.trunc));
-        const float w = a.weight[idx];
+        const float w = pf_to_float(weight[idx]);
         float tn = t;
-        if (w > 0.0f) tn = __fdiv_rn(fmaf(w, pf_decode(a.tsdf[idx]), t), w + 1.0f);
+        if (w > 0.0f) tn = __fdiv_rn(fmaf(w, pf_decode(pf_to_float(tsdf[idx])), t), w + 1.0f);
         const float wn = fminf(w + 1.0f, a.max_weight);
-        a.tsdf[idx] = pf_encode(tn, wn);
-        a.weight[idx] = wn;
+        tsdf[idx] = pf_from_float<TS>(pf_encode(tn, wn));
+        weight[idx] = pf_from_float<TW>(wn);
     }
 }
 
-__global__ void fill_kernel(float* tsdf, float* weight, size_t n)
+template <typename TS, typename TW>
+__global__ void fill_kernel(void* tsdf_, void* weight_, size_t n)
 {
+    TS* tsdf = static_cast<TS*>(tsdf_);
+    TW* weight = static_cast<TW*>(weight_);
     size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
     size_t step = (size_t)gridDim.x * blockDim.x;
     for (; i < n; i += step) {
-        tsdf[i] = PF_UNOBSERVED;
-        weight[i] = 0.0f;
+        tsdf[i] = pf_from_float<TS>(PF_UNOBSERVED);
+        weight[i] = pf_from_float<TW>(0.0f);
     }
 }
 
@@ -145,14 +152,36 @@ __global__ void fill_kernel(float* tsdf, float* weight, size_t n)
 // +x, +y, +z, so a tile is rewritten when any of those was reached by the
 // last fusion (or always, after a reset or upload).
 struct RefreshArgs {
-    const float* tsdf;
-    float4* cells;
+    const void* tsdf;
+    void* cells;
     int nx, ny, nz;
     const int* tile_stamp;
     int stamp;
     int all;
 };
 
+// One cell-view record.  Float storage: two float4 holding the corners with
+// the x-differences precomputed (v000, v100 - v000, v010, v110 - v010 |
+// v001, v101 - v001, v011, v111 - v011).  16-bit storage: the eight corner
+// values as stored (v000, v100, v010, v110 | v001, v101, v011, v111), one
+// 16-byte record; the reader forms the differences in float, so the fitness
+// sees exactly the stored grid (a difference rounded to 16 bits would not be).
+__device__ inline void store_cell(const float* p, size_t nx, size_t nxy, float* cells, size_t idx)
+{
+    const float v000 = p[0], v010 = p[nx], v001 = p[nxy], v011 = p[nxy + nx];
+    float4* c = reinterpret_cast<float4*>(cells) + 2 * idx;
+    c[0] = make_float4(v000, p[1] - v000, v010, p[nx + 1] - v010);
+    c[1] = make_float4(v001, p[nxy + 1] - v001, v011, p[nxy + nx + 1] - v011);
+}
+
+template <typename T>
+__device__ inline void store_cell(const T* p, size_t nx, size_t nxy, T* cells, size_t idx)
+{
+    const T h[8] = {p[0], p[1], p[nx], p[nx + 1], p[nxy], p[nxy + 1], p[nxy + nx], p[nxy + nx + 1]};
+    reinterpret_cast<uint4*>(cells)[idx] = *reinterpret_cast<const uint4*>(h);
+}
+
+template <typename TS>
 __global__ void __launch_bounds__(TX * TY, 4) cells_refresh_kernel(RefreshArgs a)
 {
     __shared__ int s_need;
@@ -169,18 +198,14 @@ __global__ void __launch_bounds__(TX * TY, 4) cells_refresh_kernel(RefreshArgs a
     if (!s_need) return;
     const int i = blockIdx.x * TX + threadIdx.x, j = blockIdx.y * TY + threadIdx.y;
     if (i >= a.nx - 1 || j >= a.ny - 1) return;
+    const TS* tsdf = static_cast<const TS*>(a.tsdf);
+    TS* cells = static_cast<TS*>(a.cells);
     const size_t nx = a.nx, nxy = (size_t)a.nx * a.ny;
     for (int dz = 0; dz < TZ; ++dz) {
         const int k = blockIdx.z * TZ + dz;
         if (k >= a.nz - 1) break;
         const size_t idx = i + nx * j + nxy * k;
-        const float* p = a.tsdf + idx;
-        const float v000 = p[0], v100 = p[1], v010 = p[nx], v110 = p[nx + 1];
-        const float v001 = p[nxy], v101 = p[nxy + 1], v011 = p[nxy + nx], v111 = p[nxy + nx + 1];
-        const float4 lo = make_float4(v000, v100 - v000, v010, v110 - v010);
-        const float4 hi = make_float4(v001, v101 - v001, v011, v111 - v011);
-        a.cells[2 * idx] = lo;
-        a.cells[2 * idx + 1] = hi;
+        store_cell(tsdf + idx, nx, nxy, cells, idx);
     }
 }
 
@@ -197,11 +222,49 @@ pf_status enqueue_refresh(pf_volume* v, cudaStream_t s, int all)
     r.stamp = v->stamp;
     r.all = all;
     dim3 grid(v->tiles[0], v->tiles[1], v->tiles[2]);
-    cells_refresh_kernel<<<grid, dim3(TX, TY), 0, s>>>(r);
+    switch (v->desc.tsdf_dtype) {
+    case PF_F16: cells_refresh_kernel<__half><<<grid, dim3(TX, TY), 0, s>>>(r); break;
+    case PF_BF16: cells_refresh_kernel<__nv_bfloat16><<<grid, dim3(TX, TY), 0, s>>>(r); break;
+    default: cells_refresh_kernel<float><<<grid, dim3(TX, TY), 0, s>>>(r); break;
+    }
     pf::count_launch();
     PF_LAUNCHED();
     return PF_OK;
 }
+
+// Launch a kernel templated on (tsdf storage, weight storage) for volume v.
+template <template <typename, typename> class K, typename... Args>
+void dispatch_storage(const pf_volume* v, Args&&... args)
+{
+    const bool u8 = v->desc.weight_u8 != 0;
+    switch (v->desc.tsdf_dtype) {
+    case PF_F16:
+        if (u8) K<__half, uint8_t>::run(args...); else K<__half, float>::run(args...);
+        break;
+    case PF_BF16:
+        if (u8) K<__nv_bfloat16, uint8_t>::run(args...); else K<__nv_bfloat16, float>::run(args...);
+        break;
+    default:
+        if (u8) K<float, uint8_t>::run(args...); else K<float, float>::run(args...);
+        break;
+    }
+}
+
+template <typename TS, typename TW>
+struct FillLaunch {
+    static void run(void* tsdf, void* weight, size_t n, cudaStream_t s)
+    {
+        fill_kernel<TS, TW><<<152 * 8, 256, 0, s>>>(tsdf, weight, n);
+    }
+};
+
+template <typename TS, typename TW>
+struct IntegrateLaunch {
+    static void run(dim3 grid, const IntegArgs& a, cudaStream_t s)
+    {
+        integrate_kernel<TS, TW><<<grid, dim3(TX, TY), 0, s>>>(a);
+    }
+};
 
 pf_status check_desc(const pf_volume_desc* d)
 {
@@ -215,14 +278,15 @@ pf_status check_desc(const pf_volume_desc* d)
         if (!std::isfinite(d->origin[a])) return PF_ERR_INVALID_ARG;
     if (d->max_weight < 1 || d->max_weight > 65535) return PF_ERR_INVALID_ARG;
     if (d->cell_view < -1 || d->cell_view > 1) return PF_ERR_INVALID_ARG;
-    if (d->tsdf_dtype != PF_F32 || d->weight_u8 != 0) return PF_ERR_UNSUPPORTED;
+    if (d->weight_u8 != 0 && d->weight_u8 != 1) return PF_ERR_INVALID_ARG;
+    if (d->weight_u8 && d->max_weight > 255) return PF_ERR_INVALID_ARG;
+    if (d->tsdf_dtype != PF_F32 && d->tsdf_dtype != PF_F16 && d->tsdf_dtype != PF_BF16) return PF_ERR_UNSUPPORTED;
     return PF_OK;
 }
 
 pf_status enqueue_reset(pf_volume* v, cudaStream_t s)
 {
-    int blocks = 152 * 8;
-    fill_kernel<<<blocks, 256, 0, s>>>(v->tsdf, v->weight, v->n_nodes);
+    dispatch_storage<FillLaunch>(v, v->tsdf, v->weight, v->n_nodes, s);
     pf::count_launch();
     PF_LAUNCHED();
     return enqueue_refresh(v, s, 1);
@@ -251,11 +315,12 @@ pf_status pf_create_volume(const pf_volume_desc* desc, void* stream, pf_volume**
     v->tiles[0] = (desc->nx + TX - 1) / TX;
     v->tiles[1] = (desc->ny + TY - 1) / TY;
     v->tiles[2] = (desc->nz + TZ - 1) / TZ;
-    const size_t view_bytes = v->n_nodes * 2 * sizeof(float4);
+    const size_t ts = pf_dtype_size(desc->tsdf_dtype), ws = desc->weight_u8 ? 1 : 4;
+    const size_t view_bytes = v->n_nodes * 8 * ts;
     const bool view = desc->cell_view == 1 || (desc->cell_view == 0 && view_bytes <= (16ull << 30));
     cudaError_t e = cudaGetDevice(&v->device);
-    if (e == cudaSuccess) e = cudaMalloc(&v->tsdf, v->n_nodes * sizeof(float));
-    if (e == cudaSuccess) e = cudaMalloc(&v->weight, v->n_nodes * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc(&v->tsdf, v->n_nodes * ts);
+    if (e == cudaSuccess) e = cudaMalloc(&v->weight, v->n_nodes * ws);
     if (e == cudaSuccess && view) e = cudaMalloc(&v->cells, view_bytes);
     if (e == cudaSuccess && view)
         e = cudaMalloc(&v->tile_stamp, sizeof(int) * (size_t)v->tiles[0] * v->tiles[1] * v->tiles[2]);
@@ -311,6 +376,8 @@ pf_status pf_reset_volume(pf_volume* v, void* stream)
 pf_status pf_set_fitness_variant(pf_volume* v, int variant)
 {
     if (!v || variant < 0 || variant > 11 || (variant & 3) == 3 && !v->cells) return PF_ERR_INVALID_ARG;
+    // the plain baseline exists for float tsdf and float weights only
+    if ((variant & 3) == 1 && (v->desc.tsdf_dtype != PF_F32 || v->desc.weight_u8)) return PF_ERR_INVALID_ARG;
     v->fitness_variant = variant;
     return PF_OK;
 }
@@ -318,16 +385,33 @@ pf_status pf_set_fitness_variant(pf_volume* v, int variant)
 pf_status pf_volume_upload(pf_volume* v, const float* tsdf_host, const float* weight_host)
 {
     if (!v || !tsdf_host || !weight_host) return PF_ERR_INVALID_ARG;
-    std::vector<float> enc(v->n_nodes);
-    for (size_t i = 0; i < v->n_nodes; ++i) {
-        float w = weight_host[i];
+    const size_t n = v->n_nodes;
+    const pf_dtype dt = v->desc.tsdf_dtype;
+    std::vector<float> enc(dt == PF_F32 ? n : 0);
+    std::vector<uint16_t> enc16(dt == PF_F32 ? 0 : n);
+    std::vector<uint8_t> w8(v->desc.weight_u8 ? n : 0);
+    for (size_t i = 0; i < n; ++i) {
+        const float w = weight_host[i];
         if (!(w >= 0.0f) || !std::isfinite(w) || w > (float)v->desc.max_weight) return PF_ERR_INVALID_ARG;
         if (w > 0.0f && !(std::fabs(tsdf_host[i]) <= 1.0f)) return PF_ERR_INVALID_ARG;
-        enc[i] = pf_encode(tsdf_host[i], w);
+        if (v->desc.weight_u8 && w != std::floor(w)) return PF_ERR_INVALID_ARG;
+        const float e = pf_encode(tsdf_host[i], w);
+        if (dt == PF_F32) {
+            enc[i] = e;
+        } else if (dt == PF_F16) {
+            const __half h = pf_from_float<__half>(e);
+            std::memcpy(&enc16[i], &h, 2);
+        } else {
+            const __nv_bfloat16 h = pf_from_float<__nv_bfloat16>(e);
+            std::memcpy(&enc16[i], &h, 2);
+        }
+        if (v->desc.weight_u8) w8[i] = (uint8_t)w;
     }
     PF_CUDA(cudaDeviceSynchronize());
-    PF_CUDA(cudaMemcpy(v->tsdf, enc.data(), v->n_nodes * sizeof(float), cudaMemcpyHostToDevice));
-    PF_CUDA(cudaMemcpy(v->weight, weight_host, v->n_nodes * sizeof(float), cudaMemcpyHostToDevice));
+    if (dt == PF_F32) PF_CUDA(cudaMemcpy(v->tsdf, enc.data(), n * 4, cudaMemcpyHostToDevice));
+    else PF_CUDA(cudaMemcpy(v->tsdf, enc16.data(), n * 2, cudaMemcpyHostToDevice));
+    if (v->desc.weight_u8) PF_CUDA(cudaMemcpy(v->weight, w8.data(), n, cudaMemcpyHostToDevice));
+    else PF_CUDA(cudaMemcpy(v->weight, weight_host, n * 4, cudaMemcpyHostToDevice));
     pf_status st = enqueue_refresh(v, 0, 1);
     if (st != PF_OK) return st;
     PF_CUDA(cudaDeviceSynchronize());
@@ -337,10 +421,34 @@ pf_status pf_volume_upload(pf_volume* v, const float* tsdf_host, const float* we
 pf_status pf_volume_download(const pf_volume* v, float* tsdf_host, float* weight_host)
 {
     if (!v || !tsdf_host || !weight_host) return PF_ERR_INVALID_ARG;
+    const size_t n = v->n_nodes;
+    const pf_dtype dt = v->desc.tsdf_dtype;
     PF_CUDA(cudaDeviceSynchronize());
-    PF_CUDA(cudaMemcpy(tsdf_host, v->tsdf, v->n_nodes * sizeof(float), cudaMemcpyDeviceToHost));
-    PF_CUDA(cudaMemcpy(weight_host, v->weight, v->n_nodes * sizeof(float), cudaMemcpyDeviceToHost));
-    for (size_t i = 0; i < v->n_nodes; ++i)
+    if (dt == PF_F32) {
+        PF_CUDA(cudaMemcpy(tsdf_host, v->tsdf, n * 4, cudaMemcpyDeviceToHost));
+    } else {
+        std::vector<uint16_t> raw(n);
+        PF_CUDA(cudaMemcpy(raw.data(), v->tsdf, n * 2, cudaMemcpyDeviceToHost));
+        for (size_t i = 0; i < n; ++i) {
+            if (dt == PF_F16) {
+                __half h;
+                std::memcpy(&h, &raw[i], 2);
+                tsdf_host[i] = pf_to_float(h);
+            } else {
+                __nv_bfloat16 h;
+                std::memcpy(&h, &raw[i], 2);
+                tsdf_host[i] = pf_to_float(h);
+            }
+        }
+    }
+    if (v->desc.weight_u8) {
+        std::vector<uint8_t> w8(n);
+        PF_CUDA(cudaMemcpy(w8.data(), v->weight, n, cudaMemcpyDeviceToHost));
+        for (size_t i = 0; i < n; ++i) weight_host[i] = (float)w8[i];
+    } else {
+        PF_CUDA(cudaMemcpy(weight_host, v->weight, n * 4, cudaMemcpyDeviceToHost));
+    }
+    for (size_t i = 0; i < n; ++i)
         tsdf_host[i] = weight_host[i] > 0.0f ? pf_decode(tsdf_host[i]) : 1.0f;
     return PF_OK;
 }
@@ -386,7 +494,7 @@ pf_status integrate_impl(pf_volume* v, const float* depth_dev, const pf_intrinsi
     a.stamp = ++v->stamp;
     dim3 grid(v->tiles[0], v->tiles[1], v->tiles[2]);
     pf::timing_begin(pf::KC_INTEGRATE, s);
-    integrate_kernel<<<grid, dim3(TX, TY), 0, s>>>(a);
+    dispatch_storage<IntegrateLaunch>(v, grid, a, s);
     pf::count_launch();
     pf::timing_end(pf::KC_INTEGRATE, s);
     PF_LAUNCHED();

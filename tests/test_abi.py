@@ -66,8 +66,13 @@ def test_host_side_validation_without_a_gpu(lib):
     ]
     for d in bad:
         assert lib.pf_create_volume(C.byref(d), None, C.byref(out)) == pf.PF_ERR_INVALID_ARG
-    f16 = pf.pf_volume_desc(8, 8, 8, 0.1, 0.3, (C.c_float * 3)(0, 0, 0), pf.PF_F16, 0, 255)
-    assert lib.pf_create_volume(C.byref(f16), None, C.byref(out)) == pf.PF_ERR_UNSUPPORTED
+    # storage types: 16-bit tsdf and uint8 weights exist, fp8 does not; a
+    # uint8 weight cannot count past 255
+    fp8 = pf.pf_volume_desc(8, 8, 8, 0.1, 0.3, (C.c_float * 3)(0, 0, 0), pf.PF_FP8E4M3, 0, 255)
+    assert lib.pf_create_volume(C.byref(fp8), None, C.byref(out)) == pf.PF_ERR_UNSUPPORTED
+    for dt, u8, mw in ((pf.PF_F16, 1, 256), (pf.PF_BF16, 2, 255), (pf.PF_F32, -1, 10)):
+        d = pf.pf_volume_desc(8, 8, 8, 0.1, 0.3, (C.c_float * 3)(0, 0, 0), dt, u8, mw)
+        assert lib.pf_create_volume(C.byref(d), None, C.byref(out)) == pf.PF_ERR_INVALID_ARG
     # NULL volume / pointers
     intr = pf.pf_intrinsics(4, 3, 2.0, 2.0, 1.5, 1.0, 0.1, 8.0)
     pose = (C.c_double * 16)(*[1, 0, 0, 0, 0, 1, 0, 0, 0, 0, 1, 0, 0, 0, 0, 1])
