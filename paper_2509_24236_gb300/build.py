@@ -22,6 +22,11 @@ INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",
               "--expt-relaxed-constexpr", "-I", INCLUDE]
+# Per-file flags.  track.cu: no automatic multiply-add contraction, so every
+# fused multiply-add is one written in the source and every instantiation of
+# the fitness kernel rounds the same way (the error-free products of the
+# reference transform rely on separately rounded products and sums).
+FILE_FLAGS = {"track.cu": ["--fmad=false"]}
 
 
 def nvcc() -> str:
@@ -56,7 +61,7 @@ def build(force: bool = False, verbose: bool = False, extra_flags: list | None =
 
     def compile_one(src):
         obj = os.path.join(build_dir, os.path.basename(src).replace(".cu", ".o"))
-        cmd = [cc, *ARCH, *flags, "-c", src, "-o", obj]
+        cmd = [cc, *ARCH, *flags, *FILE_FLAGS.get(os.path.basename(src), []), "-c", src, "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"nvcc failed on {src}:\n{r.stdout}\n{r.stderr}")

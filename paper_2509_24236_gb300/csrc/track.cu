@@ -18,7 +18,15 @@
 //     voxels, so the eight corner gathers of a warp fall in a handful of
 //     cache lines.  Per-particle sums are reduced with warp shuffles into
 //     per-warp shared accumulators, then per CTA into (S, C) partials in a
-//     fixed order -- no floating-point atomics, bit-reproducible.
+//     fixed order -- no floating-point atomics, bit-reproducible.  When the
+//     chunk's particles nearly coincide, lanes take particles instead and
+//     share each point through shared memory.
+//   * Samples go in pairs through Blackwell's packed f32x2 FMA / add (two
+//     float operations per instruction, rounded exactly as two scalar ones).
+//     A point whose samples under every particle of the chunk provably stay
+//     inside the grid skips the per-axis range test and forms its cell index
+//     as one linear combination.  A float cell-view record (32 bytes) is one
+//     256-bit load.
 //   * The last CTA to finish (ticket counter, no spinning) reduces the
 //     partials over point tiles and, for the search, does the selection:
 //     argmin (lowest index on ties), advantage set, its mean, the FP64 pose
@@ -31,6 +39,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <climits>
 #include <mutex>
 
 #include "pf_internal.cuh"
@@ -66,7 +75,6 @@ struct SearchState {
 constexpr int TILE_W = 8, TILE_H = 4;
 constexpr int BP_THREADS = 256, BP_TILES_PER_WARP = 8;
 constexpr int BP_CHUNK_TILES = (BP_THREADS / 32) * BP_TILES_PER_WARP;  // tiles per block
-constexpr int BP_CHUNK = BP_CHUNK_TILES * 32;                         // pixel slots per block
 
 __device__ inline int block_sum_int(int v, int* sh)
 {
@@ -296,23 +304,8 @@ struct Particle {      // shared memory, 64 bytes
     int4 m;            // magic x, y, z (cell offset folded in), unused
 };
 
-struct Xform {         // the same in registers
-    float d[9], b[3];
-    int mg[3];
-};
-
 constexpr int kMagicBits = 0x4b400000;  // bits of 1.5 * 2^23
 constexpr int kNeverValid = 0x7fffffff;  // magic of a particle that reaches no cell
-
-__device__ __forceinline__ void load_xform(const Particle& P, Xform& X)
-{
-    const float4 d0 = P.d0, d1 = P.d1, d2 = P.d2;
-    const int4 m = P.m;
-    X.d[0] = d0.x; X.d[1] = d0.y; X.d[2] = d0.z; X.b[0] = d0.w;
-    X.d[3] = d1.x; X.d[4] = d1.y; X.d[5] = d1.z; X.b[1] = d1.w;
-    X.d[6] = d2.x; X.d[7] = d2.y; X.d[8] = d2.z; X.b[2] = d2.w;
-    X.mg[0] = m.x; X.mg[1] = m.y; X.mg[2] = m.z;
-}
 
 // Camera-to-world pose of particle k in FP64.
 template <int SRC>
@@ -413,7 +406,7 @@ __device__ __forceinline__ void ref_apply(const float* Rf, float x, float y, flo
     ref_row(Rf + 6, Rf + 15, x, y, z, Yi[2], Yf[2]);
 }
 
-// Grid cell and fractions of a sample.  The grid coordinate is
+// Grid cell of a sample and its fractions.  The grid coordinate is
 // o_k + yi + (dA_k x + yf + b_k); the bracket is small and its floor comes
 // from adding 1.5*2^23 rounding down, which leaves floor() in the low
 // mantissa bits with every step exact (for |.| < 2^22).  Subtracting the
@@ -426,26 +419,6 @@ struct Cell {
     float fx, fy, fz;
     bool ok;
 };
-
-__device__ __forceinline__ Cell locate(const Xform& X, int nx, int nxy, unsigned mx, unsigned my, unsigned mz,
-                                       float x, float y, float z, const int* Yi, const float* Yf)
-{
-    const float gx = fmaf(X.d[0], x, fmaf(X.d[1], y, fmaf(X.d[2], z, Yf[0] + X.b[0])));
-    const float gy = fmaf(X.d[3], x, fmaf(X.d[4], y, fmaf(X.d[5], z, Yf[1] + X.b[1])));
-    const float gz = fmaf(X.d[6], x, fmaf(X.d[7], y, fmaf(X.d[8], z, Yf[2] + X.b[2])));
-    const float M = 12582912.0f;
-    const float rx = __fadd_rd(gx, M), ry = __fadd_rd(gy, M), rz = __fadd_rd(gz, M);
-    const int ix = __float_as_int(rx) - X.mg[0] + Yi[0];
-    const int iy = __float_as_int(ry) - X.mg[1] + Yi[1];
-    const int iz = __float_as_int(rz) - X.mg[2] + Yi[2];
-    Cell c;
-    c.ok = (unsigned)ix < mx && (unsigned)iy < my && (unsigned)iz < mz;
-    c.idx = ix + nx * iy + nxy * iz;
-    c.fx = gx - (rx - M);
-    c.fy = gy - (ry - M);
-    c.fz = gz - (rz - M);
-    return c;
-}
 
 __device__ __forceinline__ void accumulate(float t, float& s, int& c)
 {
@@ -487,9 +460,13 @@ __device__ __forceinline__ float trilerp(float fx, float fy, float fz, float v00
 // corners as stored (one 16-byte load) and the differences are formed here.
 __device__ __forceinline__ void load_cell(const float* cells, int idx, float4& lo, float4& hi)
 {
-    const float4* p = reinterpret_cast<const float4*>(cells) + 2 * (size_t)idx;
-    lo = __ldg(p);
-    hi = __ldg(p + 1);
+    // one 32-byte record, one 256-bit read-only load (records are 32-byte
+    // aligned): half the load requests of two 16-byte loads.  volatile: the
+    // load must not be hoisted above the range test that guards it.
+    const float* p = cells + 8 * (size_t)idx;
+    asm volatile("ld.global.nc.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+        : "=f"(lo.x), "=f"(lo.y), "=f"(lo.z), "=f"(lo.w), "=f"(hi.x), "=f"(hi.y), "=f"(hi.z), "=f"(hi.w)
+        : "l"(p));
 }
 
 __device__ __forceinline__ void corners_to_cell(float v000, float v100, float v010, float v110, float v001,
@@ -518,7 +495,7 @@ __device__ __forceinline__ void load_cell(const __nv_bfloat16* cells, int idx, f
                     __uint_as_float(r.w << 16), __uint_as_float(r.w & 0xffff0000u), lo, hi);
 }
 
-// One sample.  VARIANT 0: encoded tsdf nodes (non-finite nodes make the
+// Gather and accumulate one located sample.  VARIANT 0: encoded tsdf nodes (non-finite nodes make the
 // interpolated value non-finite, so validity is one comparison on the
 // result); 1: plain tsdf + weight (float), all eight nodes tested
 // explicitly; 2: the cell view.  TS is the storage type of tsdf and cells.
@@ -526,11 +503,8 @@ __device__ __forceinline__ void load_cell(const __nv_bfloat16* cells, int idx, f
 // dropped by the final predicate instead of a branch -- cheaper when almost
 // every sample lands inside, as when particles share the lanes of a warp.
 template <int VARIANT, typename TS, bool BRANCHLESS = false>
-__device__ __forceinline__ void sample(const FitArgs& a, int nx, int nxy, unsigned mx, unsigned my, unsigned mz,
-                                       const Xform& X, float x, float y, float z, const int* Yi, const float* Yf,
-                                       float& s, int& c)
+__device__ __forceinline__ void gather(const FitArgs& a, int nx, int nxy, const Cell& q, float& s, int& c)
 {
-    const Cell q = locate(X, nx, nxy, mx, my, mz, x, y, z, Yi, Yf);
     if (VARIANT == 2 && BRANCHLESS) {
         float4 lo, hi;
         load_cell(static_cast<const TS*>(a.cells), q.ok ? q.idx : 0, lo, hi);
@@ -568,6 +542,120 @@ __device__ __forceinline__ void sample(const FitArgs& a, int nx, int nxy, unsign
             c += 1;
         }
     }
+}
+
+// ---------------------------------------------------------------------------
+// Two samples at once.  Blackwell's packed f32x2 FMA / add instructions do
+// two float operations per instruction with exactly the rounding of two
+// scalar ones, so the transform, the floor and the fractions of two samples
+// cost half the issue slots and give bit-identical results.  The pair is two
+// points of one particle; the particle's values are held duplicated.
+// ---------------------------------------------------------------------------
+struct ParticleD {     // shared memory, 112 bytes
+    float4 d[6];       // (d0, d0, d1, d1), (d2, d2, d3, d3), ..., (d8, d8, b0, b0), (b1, b1, b2, b2)
+    int4 m;            // magic x, y, z and cl = -(mx + nx my + nxy mz) (wrapping)
+};
+
+struct XformD {
+    float2 d[9], b[3];
+    int mg[3];
+    int cl;
+};
+
+__device__ __forceinline__ void make_particle_d(const Particle& P, int nx, int nxy, ParticleD& D)
+{
+    const float v[12] = {P.d0.x, P.d0.y, P.d0.z, P.d1.x, P.d1.y, P.d1.z,
+                         P.d2.x, P.d2.y, P.d2.z, P.d0.w, P.d1.w, P.d2.w};
+    for (int q = 0; q < 6; ++q) D.d[q] = make_float4(v[2 * q], v[2 * q], v[2 * q + 1], v[2 * q + 1]);
+    const unsigned cl = 0u - ((unsigned)P.m.x + (unsigned)nx * (unsigned)P.m.y + (unsigned)nxy * (unsigned)P.m.z);
+    D.m = make_int4(P.m.x, P.m.y, P.m.z, (int)cl);
+}
+
+__device__ __forceinline__ void load_xformd(const ParticleD& P, XformD& X)
+{
+    float2 v[12];
+#pragma unroll
+    for (int q = 0; q < 6; ++q) {
+        const float4 f = P.d[q];
+        v[2 * q] = make_float2(f.x, f.y);
+        v[2 * q + 1] = make_float2(f.z, f.w);
+    }
+#pragma unroll
+    for (int q = 0; q < 9; ++q) X.d[q] = v[q];
+    X.b[0] = v[9];
+    X.b[1] = v[10];
+    X.b[2] = v[11];
+    X.mg[0] = P.m.x;
+    X.mg[1] = P.m.y;
+    X.mg[2] = P.m.z;
+    X.cl = P.m.w;
+}
+
+// Two points (a, b) of the same sub-tile: coordinates and reference
+// fractions as pairs, and the linear index of each reference cell,
+// yl = yi_x + nx yi_y + nxy yi_z.
+struct PointPair {
+    float2 x, y, z, yf0, yf1, yf2;
+    int yla, ylb;
+};
+
+// Cells and fractions of a pair of samples.  The packed part (transform,
+// floor, fractions) follows the grid-cell rule above for two points.  CHECKED = false:
+// the caller knows both cells lie inside the grid (the points passed the
+// chunk's interior test), so there is no range test and the cell index is
+// one linear combination, idx = yl + cl + bits(rx) + nx bits(ry) +
+// nxy bits(rz) -- the value of the per-axis form (wrapping arithmetic, exact
+// result in range).  CHECKED = true: per-axis cells from the reference cells
+// Ya, Yb and the unsigned range test.
+template <bool CHECKED>
+__device__ __forceinline__ void locate2(const XformD& X, int nx, int nxy, unsigned mx, unsigned my, unsigned mz,
+                                        const PointPair& p, const int* Ya, const int* Yb, Cell& ca, Cell& cb)
+{
+    const float2 gx = __ffma2_rn(X.d[0], p.x, __ffma2_rn(X.d[1], p.y, __ffma2_rn(X.d[2], p.z, __fadd2_rn(p.yf0, X.b[0]))));
+    const float2 gy = __ffma2_rn(X.d[3], p.x, __ffma2_rn(X.d[4], p.y, __ffma2_rn(X.d[5], p.z, __fadd2_rn(p.yf1, X.b[1]))));
+    const float2 gz = __ffma2_rn(X.d[6], p.x, __ffma2_rn(X.d[7], p.y, __ffma2_rn(X.d[8], p.z, __fadd2_rn(p.yf2, X.b[2]))));
+    const float2 M2 = make_float2(12582912.0f, 12582912.0f), nM2 = make_float2(-12582912.0f, -12582912.0f);
+    const float2 m1 = make_float2(-1.0f, -1.0f);
+    const float2 rx = __fadd2_rd(gx, M2), ry = __fadd2_rd(gy, M2), rz = __fadd2_rd(gz, M2);
+    // g - (r - M): r - M is exact, and -1 * t + g rounds once like g - t
+    const float2 fx = __ffma2_rn(__fadd2_rn(rx, nM2), m1, gx);
+    const float2 fy = __ffma2_rn(__fadd2_rn(ry, nM2), m1, gy);
+    const float2 fz = __ffma2_rn(__fadd2_rn(rz, nM2), m1, gz);
+    if (CHECKED) {
+        const int ax = __float_as_int(rx.x) - X.mg[0] + Ya[0], bx = __float_as_int(rx.y) - X.mg[0] + Yb[0];
+        const int ay = __float_as_int(ry.x) - X.mg[1] + Ya[1], by = __float_as_int(ry.y) - X.mg[1] + Yb[1];
+        const int az = __float_as_int(rz.x) - X.mg[2] + Ya[2], bz = __float_as_int(rz.y) - X.mg[2] + Yb[2];
+        ca.ok = (unsigned)ax < mx && (unsigned)ay < my && (unsigned)az < mz;
+        cb.ok = (unsigned)bx < mx && (unsigned)by < my && (unsigned)bz < mz;
+        ca.idx = ax + nx * ay + nxy * az;
+        cb.idx = bx + nx * by + nxy * bz;
+    } else {
+        const unsigned ux = (unsigned)nx, uxy = (unsigned)nxy;
+        ca.idx = (int)((unsigned)p.yla + (unsigned)X.cl + (unsigned)__float_as_int(rx.x) +
+                       ux * (unsigned)__float_as_int(ry.x) + uxy * (unsigned)__float_as_int(rz.x));
+        cb.idx = (int)((unsigned)p.ylb + (unsigned)X.cl + (unsigned)__float_as_int(rx.y) +
+                       ux * (unsigned)__float_as_int(ry.y) + uxy * (unsigned)__float_as_int(rz.y));
+        ca.ok = true;
+        cb.ok = true;
+    }
+    ca.fx = fx.x; ca.fy = fy.x; ca.fz = fz.x;
+    cb.fx = fx.y; cb.fy = fy.y; cb.fz = fz.y;
+}
+
+// Whether every sample of point (Yi, Yf) under any particle of the chunk
+// lands in a cell inside the grid: lo[a] <= yi_a <= hi[a] on every axis
+// (bounds from the chunk's reach, see the kernel) and a finite point.
+__device__ __forceinline__ bool point_interior(const int* Yi, const float* Yf, const int* lo, const int* hi)
+{
+    bool in = true;
+#pragma unroll
+    for (int q = 0; q < 3; ++q) in = in && Yi[q] >= lo[q] && Yi[q] <= hi[q] && fabsf(Yf[q]) <= 1.0f;
+    return in;
+}
+
+__device__ __forceinline__ int linear_cell(const int* Yi, int nx, int nxy)
+{
+    return (int)((unsigned)Yi[0] + (unsigned)nx * (unsigned)Yi[1] + (unsigned)nxy * (unsigned)Yi[2]);
 }
 
 // Block-wide argmin of (E, k) with the lowest k among equal E.
@@ -608,10 +696,13 @@ template <int SRC, int VARIANT, typename TS>
 __global__ void __launch_bounds__(FIT_THREADS, PF_FIT_MIN_BLOCKS) fitness_kernel(FitArgs a)
 {
     __shared__ Particle sP[KC];
+    __shared__ ParticleD sPD[KC];
     __shared__ float sRef[18];
-    // particles-on-lanes: each warp's points: (x, y, z, yi.x), (yf, yi.y), yi.z
-    __shared__ float4 sPts[FIT_WARPS][PPT * 32][2];
-    __shared__ int sYz[FIT_WARPS][PPT * 32];
+    // particles on lanes: each warp's points as pairs (point q, point q + 64
+    // of the warp): (x, y), (z, yf0), (yf1, yf2), and their reference cells
+    __shared__ float4 sPair[FIT_WARPS][PPT * 16][3];
+    __shared__ int2 sPyl[FIT_WARPS][PPT * 16];
+    __shared__ int4 sPyi[FIT_WARPS][PPT * 16][2];  // reference cells (x, y, z, -) of points a, b
     __shared__ float accS[FIT_WARPS][KC];
     __shared__ int accC[FIT_WARPS][KC];
     __shared__ int s_last;
@@ -619,10 +710,15 @@ __global__ void __launch_bounds__(FIT_THREADS, PF_FIT_MIN_BLOCKS) fitness_kernel
     __shared__ int s_mode;
     __shared__ float s_spread[2];
     __shared__ float s_red[FIT_WARPS];
+    __shared__ float s_dmax;
+    __shared__ long long s_omin[3], s_omax[3];
+    __shared__ int s_lo[3], s_hi[3];
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int k_begin = blockIdx.x * KC;
     const int kc = min(KC, a.K - k_begin);
+    const int nx = a.nx, nxy = a.nx * a.ny;
+    const unsigned mx = a.nx - 1, my = a.ny - 1, mz = a.nz - 1;
 
     if (tid == 0) {
         int skip = 0;
@@ -638,28 +734,48 @@ __global__ void __launch_bounds__(FIT_THREADS, PF_FIT_MIN_BLOCKS) fitness_kernel
     }
     __syncthreads();
     const bool skip = s_skip != 0;
-    if (!skip) build_particles<SRC>(a, k_begin, kc, sP, sRef);
+    if (!skip) {
+        build_particles<SRC>(a, k_begin, kc, sP, sRef);
+        if (tid < kc) make_particle_d(sP[tid], nx, nxy, sPD[tid]);
+    }
     __syncthreads();
     // spread of the chunk's particles relative to its first one: translation
-    // (voxels) and rotation (voxels per metre of point distance)
+    // (voxels) and rotation (voxels per metre of point distance); and the
+    // chunk's reach: the range of the particles' integer cell offsets o_k
+    // and the largest row sum of |dA_k|, which bound where any particle can
+    // put a point (see the interior test below)
     if (tid == 0) {
-        float dt = 0.0f, dr = 0.0f;
+        float dt = 0.0f, dr = 0.0f, dmax = 0.0f;
+        long long omin[3] = {LLONG_MAX, LLONG_MAX, LLONG_MAX}, omax[3] = {LLONG_MIN, LLONG_MIN, LLONG_MIN};
         if (!skip) {
             const float o0[3] = {(float)(kMagicBits - sP[0].m.x), (float)(kMagicBits - sP[0].m.y),
                                  (float)(kMagicBits - sP[0].m.z)};
             const float b0[3] = {sP[0].d0.w, sP[0].d1.w, sP[0].d2.w};
-            for (int k = 1; k < kc; ++k) {
+            for (int k = 0; k < kc; ++k) {
                 const Particle& P = sP[k];
-                dt = fmaxf(dt, fabsf((float)(kMagicBits - P.m.x) + P.d0.w - (o0[0] + b0[0])));
-                dt = fmaxf(dt, fabsf((float)(kMagicBits - P.m.y) + P.d1.w - (o0[1] + b0[1])));
-                dt = fmaxf(dt, fabsf((float)(kMagicBits - P.m.z) + P.d2.w - (o0[2] + b0[2])));
-                dr = fmaxf(dr, fabsf(P.d0.x) + fabsf(P.d0.y) + fabsf(P.d0.z));
-                dr = fmaxf(dr, fabsf(P.d1.x) + fabsf(P.d1.y) + fabsf(P.d1.z));
-                dr = fmaxf(dr, fabsf(P.d2.x) + fabsf(P.d2.y) + fabsf(P.d2.z));
+                const float4 row[3] = {P.d0, P.d1, P.d2};
+                const int m[3] = {P.m.x, P.m.y, P.m.z};
+                for (int r = 0; r < 3; ++r) {
+                    const long long o = (long long)kMagicBits - (long long)m[r];
+                    omin[r] = o < omin[r] ? o : omin[r];
+                    omax[r] = o > omax[r] ? o : omax[r];
+                    const float sum = fabsf(row[r].x) + fabsf(row[r].y) + fabsf(row[r].z);
+                    // a non-finite particle disables the interior path
+                    dmax = (sum < INFINITY && fabsf(row[r].w) <= 1.0f) ? fmaxf(dmax, sum) : INFINITY;
+                    if (k > 0) {
+                        dt = fmaxf(dt, fabsf((float)(kMagicBits - m[r]) + row[r].w - (o0[r] + b0[r])));
+                        dr = fmaxf(dr, sum);
+                    }
+                }
             }
         }
         s_spread[0] = dt;
         s_spread[1] = dr;
+        s_dmax = dmax;
+        for (int r = 0; r < 3; ++r) {
+            s_omin[r] = omin[r];
+            s_omax[r] = omax[r];
+        }
     }
     __syncthreads();
 
@@ -667,16 +783,10 @@ __global__ void __launch_bounds__(FIT_THREADS, PF_FIT_MIN_BLOCKS) fitness_kernel
     const long long Ne = N > 0 ? ((long long)N + a.stride - 1) / a.stride : 0;
     const long long beg = Ne * blockIdx.y / a.n_ptiles;
     const long long end = Ne * (blockIdx.y + 1) / a.n_ptiles;
-    const int nx = a.nx, nxy = a.nx * a.ny;
-    const unsigned mx = a.nx - 1, my = a.ny - 1, mz = a.nz - 1;
 
     if (!skip) {
-        float Rf[18];
-#pragma unroll
-        for (int q = 0; q < 18; ++q) Rf[q] = sRef[q];
         for (long long sub = beg; sub < end; sub += SUBTILE) {
-            float px[PPT], py[PPT], pz[PPT], Yf[PPT][3];
-            int Yi[PPT][3];
+            float px[PPT], py[PPT], pz[PPT];
             float r2 = 0.0f;
 #pragma unroll
             for (int p = 0; p < PPT; ++p) {
@@ -692,7 +802,6 @@ __global__ void __launch_bounds__(FIT_THREADS, PF_FIT_MIN_BLOCKS) fitness_kernel
                     py[p] = NAN;
                     pz[p] = NAN;
                 }
-                ref_apply(Rf, px[p], py[p], pz[p], Yi[p], Yf[p]);
             }
             // mapping of this sub-tile: when every particle puts a point in
             // (nearly) the same cell, lanes take particles and share a point,
@@ -704,48 +813,137 @@ __global__ void __launch_bounds__(FIT_THREADS, PF_FIT_MIN_BLOCKS) fitness_kernel
             if (tid == 0) {
                 float m = 0.0f;
                 for (int w = 0; w < FIT_WARPS; ++w) m = fmaxf(m, s_red[w]);
+                const float rad = sqrtf(m);
                 // (a chunk of fewer than 24 particles would leave lanes idle)
-                s_mode = kc >= 24 && (s_spread[0] + s_spread[1] * sqrtf(m)) < a.pm_threshold;
+                s_mode = kc >= 24 && (s_spread[0] + s_spread[1] * rad) < a.pm_threshold;
+                // Interior test.  Sample cell coordinate on axis r:
+                // yi_r + o_k,r + floor(dA_k,r . x + yf_r + b_k,r) with
+                // |yf| <= 1/2 + eps, 0 <= b < 1 and |dA_k,r . x| <= dmax |x|,
+                // so it lies within yi_r + [omin_r - E, omax_r + E] for
+                // E = ceil(dmax |x|) + 3 (one cell of margin).  A point whose
+                // yi_r keeps that range inside [0, n_r - 2] on every axis
+                // needs no range test under any particle of the chunk.
+                const float reach = s_dmax * rad;
+                const long long E = reach < 1.0e6f ? (long long)ceilf(reach) + 3 : (1ll << 40);
+                const int n[3] = {a.nx, a.ny, a.nz};
+                for (int r = 0; r < 3; ++r) {
+                    const long long lo = E - s_omin[r], hi = (long long)(n[r] - 2) - E - s_omax[r];
+                    s_lo[r] = (int)(lo > INT_MAX ? INT_MAX : (lo < INT_MIN ? INT_MIN : lo));
+                    s_hi[r] = (int)(hi < INT_MIN ? INT_MIN : (hi > INT_MAX ? INT_MAX : hi));
+                }
             }
             __syncthreads();
+            const int lo[3] = {s_lo[0], s_lo[1], s_lo[2]}, hi[3] = {s_hi[0], s_hi[1], s_hi[2]};
+            // reference products, interior flags and pairs (point p, point p + 2)
+            PointPair P2[PPT / 2];
+            int Yi[PPT][3];
+            bool in_all = true;
+#pragma unroll
+            for (int h = 0; h < PPT / 2; ++h) {
+                int* Ya = Yi[h];
+                int* Yb = Yi[h + 2];
+                float Fa[3], Fb[3];
+                ref_apply(sRef, px[h], py[h], pz[h], Ya, Fa);
+                ref_apply(sRef, px[h + 2], py[h + 2], pz[h + 2], Yb, Fb);
+                const bool ia = point_interior(Ya, Fa, lo, hi), ib = point_interior(Yb, Fb, lo, hi);
+                in_all = in_all && ia && ib;
+                P2[h].x = make_float2(px[h], px[h + 2]);
+                P2[h].y = make_float2(py[h], py[h + 2]);
+                P2[h].z = make_float2(pz[h], pz[h + 2]);
+                P2[h].yf0 = make_float2(Fa[0], Fb[0]);
+                P2[h].yf1 = make_float2(Fa[1], Fb[1]);
+                P2[h].yf2 = make_float2(Fa[2], Fb[2]);
+                P2[h].yla = (ia && ib) ? linear_cell(Ya, nx, nxy) : INT_MIN;
+                P2[h].ylb = linear_cell(Yb, nx, nxy);
+            }
             if (!s_mode) {
-                for (int kk = 0; kk < kc; ++kk) {
-                    Xform X;
-                    load_xform(sP[kk], X);
-                    float s = 0.0f;
-                    int c = 0;
+                if (__all_sync(0xffffffffu, in_all)) {
+                    for (int kk = 0; kk < kc; ++kk) {
+                        XformD X;
+                        load_xformd(sPD[kk], X);
+                        float s = 0.0f;
+                        int c = 0;
 #pragma unroll
-                    for (int p = 0; p < PPT; ++p)
-                        sample<VARIANT, TS>(a, nx, nxy, mx, my, mz, X, px[p], py[p], pz[p], Yi[p], Yf[p], s, c);
+                        for (int h = 0; h < PPT / 2; ++h) {
+                            Cell ca, cb;
+                            locate2<false>(X, nx, nxy, mx, my, mz, P2[h], nullptr, nullptr, ca, cb);
+                            gather<VARIANT, TS, true>(a, nx, nxy, ca, s, c);
+                            gather<VARIANT, TS, true>(a, nx, nxy, cb, s, c);
+                        }
+                        c = __reduce_add_sync(0xffffffffu, c);
 #pragma unroll
-                    for (int o = 16; o > 0; o >>= 1) {
-                        s += __shfl_xor_sync(0xffffffffu, s, o);
-                        c += __shfl_xor_sync(0xffffffffu, c, o);
+                        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+                        if (lane == 0) {
+                            accS[warp][kk] += s;
+                            accC[warp][kk] += c;
+                        }
                     }
-                    if (lane == 0) {
-                        accS[warp][kk] += s;
-                        accC[warp][kk] += c;
+                } else {
+                    // some point of the warp may leave the grid: per-sample
+                    // range tests
+                    for (int kk = 0; kk < kc; ++kk) {
+                        XformD X;
+                        load_xformd(sPD[kk], X);
+                        float s = 0.0f;
+                        int c = 0;
+#pragma unroll
+                        for (int h = 0; h < PPT / 2; ++h) {
+                            Cell ca, cb;
+                            locate2<true>(X, nx, nxy, mx, my, mz, P2[h], Yi[h], Yi[h + 2], ca, cb);
+                            gather<VARIANT, TS, true>(a, nx, nxy, ca, s, c);
+                            gather<VARIANT, TS, true>(a, nx, nxy, cb, s, c);
+                        }
+                        c = __reduce_add_sync(0xffffffffu, c);
+#pragma unroll
+                        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+                        if (lane == 0) {
+                            accS[warp][kk] += s;
+                            accC[warp][kk] += c;
+                        }
                     }
                 }
             } else {
+                // the warp's 128 points as 64 pairs: pair h * 32 + lane holds
+                // this lane's points h and h + 2
 #pragma unroll
-                for (int p = 0; p < PPT; ++p) {
-                    sPts[warp][p * 32 + lane][0] = make_float4(px[p], py[p], pz[p], __int_as_float(Yi[p][0]));
-                    sPts[warp][p * 32 + lane][1] = make_float4(Yf[p][0], Yf[p][1], Yf[p][2], __int_as_float(Yi[p][1]));
-                    sYz[warp][p * 32 + lane] = Yi[p][2];
+                for (int h = 0; h < PPT / 2; ++h) {
+                    const int j = h * 32 + lane;
+                    sPair[warp][j][0] = make_float4(P2[h].x.x, P2[h].x.y, P2[h].y.x, P2[h].y.y);
+                    sPair[warp][j][1] = make_float4(P2[h].z.x, P2[h].z.y, P2[h].yf0.x, P2[h].yf0.y);
+                    sPair[warp][j][2] = make_float4(P2[h].yf1.x, P2[h].yf1.y, P2[h].yf2.x, P2[h].yf2.y);
+                    sPyl[warp][j] = make_int2(P2[h].yla, P2[h].ylb);
+                    sPyi[warp][j][0] = make_int4(Yi[h][0], Yi[h][1], Yi[h][2], 0);
+                    sPyi[warp][j][1] = make_int4(Yi[h + 2][0], Yi[h + 2][1], Yi[h + 2][2], 0);
                 }
                 __syncwarp();
-                Xform X;
-                load_xform(sP[lane < kc ? lane : 0], X);
+                const int kl = lane < kc ? lane : 0;
+                XformD X;
+                load_xformd(sPD[kl], X);
                 float s = 0.0f;
                 int c = 0;
 #pragma unroll 2
-                for (int q = 0; q < PPT * 32; ++q) {
-                    const float4 xp = sPts[warp][q][0];
-                    const float4 yp = sPts[warp][q][1];
-                    const int yi[3] = {__float_as_int(xp.w), __float_as_int(yp.w), sYz[warp][q]};
-                    const float yf[3] = {yp.x, yp.y, yp.z};
-                    sample<VARIANT, TS, true>(a, nx, nxy, mx, my, mz, X, xp.x, xp.y, xp.z, yi, yf, s, c);
+                for (int j = 0; j < PPT * 16; ++j) {
+                    const float4 q0 = sPair[warp][j][0], q1 = sPair[warp][j][1], q2 = sPair[warp][j][2];
+                    const int2 yl = sPyl[warp][j];
+                    PointPair pp;
+                    pp.x = make_float2(q0.x, q0.y);
+                    pp.y = make_float2(q0.z, q0.w);
+                    pp.z = make_float2(q1.x, q1.y);
+                    pp.yf0 = make_float2(q1.z, q1.w);
+                    pp.yf1 = make_float2(q2.x, q2.y);
+                    pp.yf2 = make_float2(q2.z, q2.w);
+                    pp.yla = yl.x;
+                    pp.ylb = yl.y;
+                    Cell ca, cb;
+                    if (yl.x != INT_MIN) {  // the same for every lane
+                        locate2<false>(X, nx, nxy, mx, my, mz, pp, nullptr, nullptr, ca, cb);
+                    } else {
+                        const int4 ya = sPyi[warp][j][0], yb = sPyi[warp][j][1];
+                        const int Ya[3] = {ya.x, ya.y, ya.z}, Yb[3] = {yb.x, yb.y, yb.z};
+                        locate2<true>(X, nx, nxy, mx, my, mz, pp, Ya, Yb, ca, cb);
+                    }
+                    gather<VARIANT, TS, true>(a, nx, nxy, ca, s, c);
+                    gather<VARIANT, TS, true>(a, nx, nxy, cb, s, c);
                 }
                 __syncwarp();
                 if (lane < kc) {
