@@ -413,16 +413,25 @@ def run_ours(args):
     return 0
 
 
+def fitness_source_sha() -> str:
+    """sha256 prefix of the fitness kernel's sources, as recorded beside the
+    committed ncu capture."""
+    import hashlib
+    h = hashlib.sha256()
+    for name in ("track.cu", "pf_internal.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_2509_24236_gb300", "csrc", name), "rb").read())
+    return h.hexdigest()[:16]
+
+
 def committed_traffic():
     """DRAM bytes per launch of the fitness kernel from the committed ncu
-    summary, or None when csrc/track.cu has changed since that capture."""
-    import hashlib
+    summary, or None when the kernel's sources (csrc/track.cu and
+    csrc/pf_internal.cuh) have changed since that capture."""
     import re
     path = os.path.join(ROOT, "profiles", "fitness_kernel_multiroom.md")
-    src = os.path.join(ROOT, "paper_2509_24236_gb300", "csrc", "track.cu")
     try:
         text = open(path).read()
-        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        sha = fitness_source_sha()
     except OSError:
         return None
     m = re.search(r"traffic_bytes_per_launch:\s*(\d+)", text)

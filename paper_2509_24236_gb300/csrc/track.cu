@@ -921,7 +921,7 @@ __global__ void __launch_bounds__(FIT_THREADS, PF_FIT_MIN_BLOCKS) fitness_kernel
                 load_xformd(sPD[kl], X);
                 float s = 0.0f;
                 int c = 0;
-#pragma unroll 2
+#pragma unroll 4
                 for (int j = 0; j < PPT * 16; ++j) {
                     const float4 q0 = sPair[warp][j][0], q1 = sPair[warp][j][1], q2 = sPair[warp][j][2];
                     const int2 yl = sPyl[warp][j];
