@@ -92,6 +92,12 @@ def _load():
                                      C.POINTER(C.c_ubyte), C.c_double, C.c_double]
         lib.or_raycast.restype = None
         lib.or_raycast.argtypes = [dp, dp, C.POINTER(_Grid), C.POINTER(_Intr), dp, C.c_double, dp, dp]
+        lib.or_perturb_pose.restype = None
+        lib.or_perturb_pose.argtypes = [dp, dp, dp]
+        lib.or_align_loss.restype = None
+        lib.or_align_loss.argtypes = [dp, dp, C.POINTER(_Grid), dp, C.c_long, dp, dp, dp, lp, dp, dp]
+        lib.or_polish.restype = C.c_int
+        lib.or_polish.argtypes = [dp, dp, C.POINTER(_Grid), dp, C.c_long, dp, C.c_int, dp]
         lib.or_num_threads.restype = C.c_int
         _lib = lib
     return _lib
@@ -273,3 +279,51 @@ def raycast(vol: Volume, intr, pose, step: float | None = None):
                        C.byref(_intr(intr)), _p(_pose12(pose), C.c_double), float(step),
                        _p(depth, C.c_double), _p(normals, C.c_double))
     return depth, normals
+
+
+# ---------------------------------------------------------------------------
+# Alignment loss, its derivatives and the Gauss-Newton polish
+# ---------------------------------------------------------------------------
+
+def perturb_pose(P, xi) -> np.ndarray:
+    """4x4 pose of q = Exp(omega) (R x + t) + v, xi = (omega, v)."""
+    out = np.empty(12)
+    _load().or_perturb_pose(_p(_pose12(P), C.c_double), _p(_f64(xi), C.c_double), _p(out, C.c_double))
+    T = np.eye(4)
+    T[:3, :4] = out.reshape(3, 4)
+    return T
+
+
+@dataclass
+class AlignResult:
+    loss: float            # sum of tsdf^2 over the valid points
+    count: int             # valid points
+    grad_xi: np.ndarray    # dL/dxi at xi (6)
+    grad_tsdf: np.ndarray | None  # dL/dV per node, or None
+
+
+def align_loss(vol: Volume, points, pose, xi=None, grad_tsdf: bool = False) -> AlignResult:
+    pts = _f64(np.asarray(points)[:, :3])
+    gV = np.zeros(vol.grid.n_nodes) if grad_tsdf else None
+    L = C.c_double()
+    Cn = C.c_long()
+    g = np.empty(6)
+    _load().or_align_loss(_p(vol.tsdf, C.c_double), _p(vol.weight, C.c_double), C.byref(vol._g()),
+                          _p(pts, C.c_double), pts.shape[0], _p(_pose12(pose), C.c_double),
+                          _p(_f64(xi), C.c_double) if xi is not None else None, C.byref(L), C.byref(Cn),
+                          _p(g, C.c_double), _p(gV, C.c_double) if gV is not None else None)
+    return AlignResult(L.value, Cn.value, g, gV)
+
+
+def polish(vol: Volume, points, pose, steps: int = 10):
+    """(pose 4x4 after `steps` damped Gauss-Newton candidates, accepted
+    steps, objective trace of steps + 1 values)."""
+    pts = _f64(np.asarray(points)[:, :3])
+    T = _pose12(pose).copy()
+    trace = np.empty(steps + 1)
+    acc = _load().or_polish(_p(vol.tsdf, C.c_double), _p(vol.weight, C.c_double), C.byref(vol._g()),
+                            _p(pts, C.c_double), pts.shape[0], _p(T, C.c_double), int(steps),
+                            _p(trace, C.c_double))
+    P = np.eye(4)
+    P[:3, :4] = T.reshape(3, 4)
+    return P, int(acc), trace

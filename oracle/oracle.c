@@ -502,6 +502,247 @@ int or_track(const double* tsdf, const double* weight, const or_grid* g,
 }
 
 /* ------------------------------------------------------------------------ */
+/* Alignment loss and its derivatives (gradient refinement of a pose found  */
+/* by the search; the residual is the TSDF of Sec. III-B, squared).          */
+/* ------------------------------------------------------------------------ */
+/* reading: the loss of pose T over points x_j is L(T) = sum over the points
+ * falling in valid cells of tsdf(T x_j)^2 (tsdf normalised by tau, validity
+ * as in the fitness).  A pose is perturbed as
+ *     q = Exp(omega) (R x + t) + v,       xi = (omega, v),
+ * so dq/dv = I and, with Exp(omega + d) = Exp(J_l(omega) d) Exp(omega) (J_l
+ * the left Jacobian of SO(3)), dq/domega = -[q - v]x J_l(omega); at xi = 0
+ * this is the usual left perturbation dq/dxi = [-[q]x | I].  With grad t the
+ * gradient of the trilinear interpolant in metres:
+ *     dL/dv     = sum 2 t grad t,
+ *     dL/domega = J_l(omega)^T sum 2 t ((q - v) x grad t).
+ * dL/dV_n = sum 2 t w_n(q) over the samples whose cell has node n (w_n its
+ * trilinear weight): the derivative with respect to the stored tsdf value of
+ * node n, at fixed cell validity. */
+
+/* value, gradient in grid units (d t / d g), lower cell corner and
+ * fractions of the valid cell containing q; 0 when q is in no valid cell */
+static int sample_grad(const double* tsdf, const double* weight, const or_grid* g, const double q[3],
+                       double* val, double dg[3], long i0[3], double f[3], double v[8])
+{
+    double gc[3];
+    int n[3] = {g->nx, g->ny, g->nz};
+    for (int a = 0; a < 3; ++a) {
+        gc[a] = (q[a] - g->origin[a]) / g->voxel_size;
+        if (!(gc[a] >= 0.0 && gc[a] < (double)(n[a] - 1))) return 0;
+        i0[a] = (long)floor(gc[a]);
+        f[a] = gc[a] - (double)i0[a];
+    }
+    for (int c = 0; c < 8; ++c) {
+        size_t idx = node_index(g, i0[0] + (c & 1), i0[1] + ((c >> 1) & 1), i0[2] + ((c >> 2) & 1));
+        if (!(weight[idx] > 0.0) || !(fabs(tsdf[idx]) < 1.0)) return 0;
+        v[c] = tsdf[idx];
+    }
+    double x00 = v[0] + f[0] * (v[1] - v[0]);
+    double x10 = v[2] + f[0] * (v[3] - v[2]);
+    double x01 = v[4] + f[0] * (v[5] - v[4]);
+    double x11 = v[6] + f[0] * (v[7] - v[6]);
+    double y0 = x00 + f[1] * (x10 - x00);
+    double y1 = x01 + f[1] * (x11 - x01);
+    *val = y0 + f[2] * (y1 - y0);
+    /* partial derivatives of the nested linear interpolations */
+    double dx00 = v[1] - v[0], dx10 = v[3] - v[2], dx01 = v[5] - v[4], dx11 = v[7] - v[6];
+    double dy0 = dx00 + f[1] * (dx10 - dx00), dy1 = dx01 + f[1] * (dx11 - dx01);
+    dg[0] = dy0 + f[2] * (dy1 - dy0);
+    dg[1] = (x10 - x00) + f[2] * ((x11 - x01) - (x10 - x00));
+    dg[2] = y1 - y0;
+    return 1;
+}
+
+/* left Jacobian of SO(3): I + (1 - cos th)/th^2 [w]x + (th - sin th)/th^3 [w]x^2 */
+static void so3_left_jacobian(const double w[3], double J[9])
+{
+    double th2 = w[0] * w[0] + w[1] * w[1] + w[2] * w[2];
+    double th = sqrt(th2);
+    double a, b;
+    if (th < 1e-6) {
+        a = 0.5 - th2 / 24.0;
+        b = 1.0 / 6.0 - th2 / 120.0;
+    } else {
+        a = (1.0 - cos(th)) / th2;
+        b = (th - sin(th)) / (th2 * th);
+    }
+    double K[9] = {0.0, -w[2], w[1], w[2], 0.0, -w[0], -w[1], w[0], 0.0};
+    for (int r = 0; r < 3; ++r)
+        for (int c = 0; c < 3; ++c) {
+            double kk = 0.0;
+            for (int m = 0; m < 3; ++m) kk += K[3 * r + m] * K[3 * m + c];
+            J[3 * r + c] = (r == c ? 1.0 : 0.0) + a * K[3 * r + c] + b * kk;
+        }
+}
+
+/* The pose q = Exp(omega) (R x + t) + v as a row-major 3x4 transform. */
+void or_perturb_pose(const double T[12], const double xi[6], double out[12])
+{
+    double dR[9];
+    or_so3_exp(xi, dR);
+    compose(dR, xi + 3, T, 0, out);
+}
+
+/* Loss, valid count, dL/dxi (6) at xi, and dL/dV accumulated into gV
+ * (n_nodes, may be NULL) for one pose T perturbed by xi (may be NULL). */
+void or_align_loss(const double* tsdf, const double* weight, const or_grid* g, const double* pts, long n,
+                   const double T[12], const double* xi, double* L, long* C, double grad_xi[6], double* gV)
+{
+    double Tp[12], zero[6] = {0, 0, 0, 0, 0, 0};
+    const double* x6 = xi ? xi : zero;
+    or_perturb_pose(T, x6, Tp);
+    double loss = 0.0, gw[3] = {0, 0, 0}, gv[3] = {0, 0, 0};
+    long c = 0;
+    for (long j = 0; j < n; ++j) {
+        double q[3], t, dg[3], f[3], v[8];
+        long i0[3];
+        transform(Tp, pts + 3 * j, q);
+        if (!sample_grad(tsdf, weight, g, q, &t, dg, i0, f, v)) continue;
+        loss += t * t;
+        c += 1;
+        double gt[3] = {dg[0] / g->voxel_size, dg[1] / g->voxel_size, dg[2] / g->voxel_size};
+        double r[3] = {q[0] - x6[3], q[1] - x6[4], q[2] - x6[5]};
+        double cr[3] = {r[1] * gt[2] - r[2] * gt[1], r[2] * gt[0] - r[0] * gt[2], r[0] * gt[1] - r[1] * gt[0]};
+        for (int a = 0; a < 3; ++a) {
+            gw[a] += 2.0 * t * cr[a];
+            gv[a] += 2.0 * t * gt[a];
+        }
+        if (gV)
+            for (int cc = 0; cc < 8; ++cc) {
+                double w = ((cc & 1) ? f[0] : 1.0 - f[0]) * (((cc >> 1) & 1) ? f[1] : 1.0 - f[1]) *
+                           (((cc >> 2) & 1) ? f[2] : 1.0 - f[2]);
+                gV[node_index(g, i0[0] + (cc & 1), i0[1] + ((cc >> 1) & 1), i0[2] + ((cc >> 2) & 1))] +=
+                    2.0 * t * w;
+            }
+    }
+    double J[9];
+    so3_left_jacobian(x6, J);
+    for (int a = 0; a < 3; ++a) {
+        grad_xi[a] = J[a] * gw[0] + J[3 + a] * gw[1] + J[6 + a] * gw[2];  /* J^T gw */
+        grad_xi[3 + a] = gv[a];
+    }
+    *L = loss;
+    *C = c;
+}
+
+/* reading: the refinement after the search is a damped Gauss-Newton
+ * (Levenberg-Marquardt) on the residuals r_j = tsdf(T x_j) over the valid
+ * points: J_j = grad t^T [-[q]x | I], H = sum J_j^T J_j, b = sum J_j^T r_j;
+ * the step solves (H + lambda diag(H)) d = -b and the candidate is
+ * [Exp(d_omega) | d_v] applied on the left of T.  The objective is the mean
+ * squared residual over the valid points; a candidate is accepted only when
+ * it lowers it (then lambda /= 10), otherwise it is dropped and
+ * lambda *= 10.  lambda starts at 1e-3; `steps` candidates are tried.
+ * trace[0] = objective at T, trace[s] = objective after step s.  Returns the
+ * number of accepted steps; T is updated in place. */
+static void gn_system(const double* tsdf, const double* weight, const or_grid* g, const double* pts, long n,
+                      const double T[12], double H[36], double b[6], double* L, long* C)
+{
+    memset(H, 0, 36 * sizeof(double));
+    memset(b, 0, 6 * sizeof(double));
+    double loss = 0.0;
+    long c = 0;
+    for (long j = 0; j < n; ++j) {
+        double q[3], t, dg[3], f[3], v[8];
+        long i0[3];
+        transform(T, pts + 3 * j, q);
+        if (!sample_grad(tsdf, weight, g, q, &t, dg, i0, f, v)) continue;
+        double gt[3] = {dg[0] / g->voxel_size, dg[1] / g->voxel_size, dg[2] / g->voxel_size};
+        double Jr[6] = {q[1] * gt[2] - q[2] * gt[1], q[2] * gt[0] - q[0] * gt[2], q[0] * gt[1] - q[1] * gt[0],
+                        gt[0], gt[1], gt[2]};
+        for (int r = 0; r < 6; ++r) {
+            b[r] += Jr[r] * t;
+            for (int cc = 0; cc < 6; ++cc) H[6 * r + cc] += Jr[r] * Jr[cc];
+        }
+        loss += t * t;
+        c += 1;
+    }
+    *L = loss;
+    *C = c;
+}
+
+/* solve the 6x6 system A d = y by Gaussian elimination with partial
+ * pivoting; 0 when singular */
+static int solve6(const double A_in[36], const double y_in[6], double d[6])
+{
+    double A[36], y[6];
+    memcpy(A, A_in, sizeof(A));
+    memcpy(y, y_in, sizeof(y));
+    for (int col = 0; col < 6; ++col) {
+        int piv = col;
+        for (int r = col + 1; r < 6; ++r)
+            if (fabs(A[6 * r + col]) > fabs(A[6 * piv + col])) piv = r;
+        if (!(fabs(A[6 * piv + col]) > 0.0)) return 0;
+        if (piv != col) {
+            for (int cc = 0; cc < 6; ++cc) {
+                double tmp = A[6 * col + cc];
+                A[6 * col + cc] = A[6 * piv + cc];
+                A[6 * piv + cc] = tmp;
+            }
+            double tmp = y[col];
+            y[col] = y[piv];
+            y[piv] = tmp;
+        }
+        for (int r = col + 1; r < 6; ++r) {
+            double m = A[6 * r + col] / A[6 * col + col];
+            for (int cc = col; cc < 6; ++cc) A[6 * r + cc] -= m * A[6 * col + cc];
+            y[r] -= m * y[col];
+        }
+    }
+    for (int r = 5; r >= 0; --r) {
+        double acc = y[r];
+        for (int cc = r + 1; cc < 6; ++cc) acc -= A[6 * r + cc] * d[cc];
+        d[r] = acc / A[6 * r + r];
+    }
+    return 1;
+}
+
+int or_polish(const double* tsdf, const double* weight, const or_grid* g, const double* pts, long n,
+              double T[12], int steps, double* trace)
+{
+    double H[36], b[6], L;
+    long C;
+    double lambda = 1e-3;
+    int accepted = 0;
+    gn_system(tsdf, weight, g, pts, n, T, H, b, &L, &C);
+    double obj = C > 0 ? L / (double)C : INFINITY;
+    if (trace) trace[0] = obj;
+    for (int st = 0; st < steps; ++st) {
+        double A[36], y[6], d[6], Tc[12];
+        int ok = C > 0;
+        if (ok) {
+            for (int r = 0; r < 36; ++r) A[r] = H[r];
+            for (int r = 0; r < 6; ++r) {
+                A[7 * r] += lambda * H[7 * r];
+                y[r] = -b[r];
+            }
+            ok = solve6(A, y, d);
+        }
+        if (ok) {
+            or_perturb_pose(T, d, Tc);
+            double Hc[36], bc[6], Lc;
+            long Cc;
+            gn_system(tsdf, weight, g, pts, n, Tc, Hc, bc, &Lc, &Cc);
+            double objc = Cc > 0 ? Lc / (double)Cc : INFINITY;
+            if (objc < obj) {
+                memcpy(T, Tc, sizeof(Tc));
+                memcpy(H, Hc, sizeof(Hc));
+                memcpy(b, bc, sizeof(bc));
+                L = Lc;
+                C = Cc;
+                obj = objc;
+                lambda /= 10.0;
+                ++accepted;
+            } else {
+                lambda *= 10.0;
+            }
+        }
+        if (trace) trace[st + 1] = obj;
+    }
+    return accepted;
+}
+
+/* ------------------------------------------------------------------------ */
 /* Fusion "the same as KinectFusion" (Sec. III): projective TSDF update.     */
 /* ------------------------------------------------------------------------ */
 /* reading: for node X_w, X_c = R^T (X_w - t); with z_c > 0 it projects to
