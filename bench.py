@@ -60,8 +60,10 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ref-particles", type=int, default=192,
                     help="particles per reference-arm step (a bounded slice of one iteration)")
-    ap.add_argument("--kernel", default=None, choices=["fitness", "integrate"],
-                    help="time one kernel on the multiroom volume instead of the frame loop (profiling)")
+    ap.add_argument("--kernel", default=None, choices=["fitness", "integrate", "align"],
+                    help="time one kernel on the multiroom volume instead of the frame loop (profiling); "
+                         "align: loss + pose and node gradients of 64 320x240 frames against a 256^3 volume, "
+                         "and the 10-step polish")
     ap.add_argument("--spread", type=float, default=3.0,
                     help="--kernel fitness: poses perturbed up to this many degrees and centimetres")
     ap.add_argument("--reps", type=int, default=3, help="--kernel: timed launches after one warm-up launch")
@@ -559,8 +561,98 @@ def run_kernel(args):
     return 0
 
 
+ALIGN_FRAMES = 64
+
+
+def align_sequence(seed: int):
+    """64 frames of 320x240 against a 256^3 TSDF at 2 cm (tau 6 cm) of the
+    multiroom scene, every 4th frame of its trajectory."""
+    import synth
+    intr = synth.Intrinsics(320, 240, 262.5, 262.5, 159.5, 119.5, 0.1, 8.0)
+    grid = synth.Grid(256, 256, 256, 0.02, 0.06, (0.0, 0.0, 0.0))
+    return synth.multiroom_sequence(300, seed, grid=grid, intr=intr)
+
+
+def _render_align(args):
+    seed, f = args
+    return align_sequence(seed).depth(f)
+
+
+def run_align(args):
+    """Alignment loss with pose and node-value gradients (pf_align_loss) for
+    64 frames at once, each at its true pose perturbed by 1 deg / 1 cm, and
+    the 10-step Gauss-Newton polish (pf_polish) of one frame.  Prints one
+    JSON line."""
+    import multiprocessing as mp
+    frames = [4 * i for i in range(ALIGN_FRAMES)]
+    with mp.get_context("spawn").Pool(max(1, min(16, (os.cpu_count() or 2) - 1))) as pool:
+        depths = pool.map(_render_align, [(args.seed, f) for f in frames])
+    import torch
+
+    import paper_2509_24236_gb300 as pf
+    import synth
+    from paper_2509_24236_gb300 import build as pfbuild
+    pfbuild.build()
+    pf.load()
+    dev = torch.device("cuda", 0)
+    seq = align_sequence(args.seed)
+    intr = seq.intr
+    vol = new_volume(pf, seq.grid, args)
+    n_max = intr.width * intr.height
+    pts = torch.empty((ALIGN_FRAMES, n_max, 4), dtype=torch.float32, device=dev)
+    counts = torch.empty(ALIGN_FRAMES, dtype=torch.int32, device=dev)
+    for i, f in enumerate(frames):
+        d = torch.from_numpy(depths[i]).to(dev)
+        vol.integrate(d, intr, seq.gt[f])
+        p, n = pf.backproject(d, intr)
+        pts[i].copy_(p)
+        counts[i:i + 1].copy_(n)
+    u = synth.uniform01(91, 2 * ALIGN_FRAMES)
+    poses = torch.from_numpy(np.stack([seq.gt[f] @ synth.perturbation(92, i, 1.0 * u[2 * i], 1.0 * u[2 * i + 1])
+                                       for i, f in enumerate(frames)])).to(dev)
+    call = lambda: vol.align_loss(pts, poses, counts=counts, grad_xi=True, grad_tsdf=True)
+    call()
+    torch.cuda.synchronize()
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(args.reps):
+        loss, cnt, gx, gv = call()
+    b.record()
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b) / args.reps
+    samples = int(counts.sum().item())
+    # polish of frame 0 from its perturbed pose
+    pose0 = poses[0].reshape(16).clone()
+    vol.polish(pts[0], pose0, steps=10, n_dev=counts[0:1])
+    torch.cuda.synchronize()
+    a.record()
+    for _ in range(args.reps):
+        pose0.copy_(poses[0].reshape(16))
+        trace, acc = vol.polish(pts[0], pose0, steps=10, n_dev=counts[0:1])
+    b.record()
+    torch.cuda.synchronize()
+    ms_polish = a.elapsed_time(b) / args.reps
+    P0 = pose0.cpu().numpy().reshape(4, 4)
+    print(json.dumps({
+        "kernel": "align", "storage": storage_desc(args), "frames": ALIGN_FRAMES, "resolution": "320x240",
+        "volume": "256^3 @ 2 cm, tau 6 cm", "reps": args.reps, "points": samples,
+        "ms_per_call": ms, "frames_per_s": ALIGN_FRAMES / (ms / 1e3), "samples_per_s": samples / (ms / 1e3),
+        "valid_fraction": float(cnt.sum().item()) / max(1, samples),
+        "polish": {"steps": 10, "ms": ms_polish, "accepted": int(acc.item()),
+                   "objective_first_last": [float(trace[0]), float(trace[-1])],
+                   "trans_err_cm_before_after": [100 * float(np.linalg.norm(poses[0].cpu().numpy()[:3, 3] -
+                                                                           seq.gt[frames[0]][:3, 3])),
+                                                 100 * float(np.linalg.norm(P0[:3, 3] - seq.gt[frames[0]][:3, 3]))]},
+    }))
+    vol.close()
+    return 0
+
+
 def main():
     args = parse()
+    if args.kernel == "align":
+        return run_align(args)
     if args.kernel:
         return run_kernel(args)
     if args.impl == "reference":

@@ -260,6 +260,57 @@ PF_API pf_status pf_track_reserve(pf_volume* vol, int max_pixels, int k_max);
 PF_API pf_status pf_raycast(const pf_volume* vol, const pf_intrinsics* intr, const double cam_to_world[16],
                      float* depth_out_dev, float* normal_out_dev_or_null, void* cuda_stream);
 
+/* Alignment loss of n_frames poses against their frames' points, and its
+ * derivatives -- the gradient counterpart of the fitness (Sec. III-B: the
+ * residual of a point is the TSDF at the transformed point, normalised by
+ * tau and trilinear, defined when the point falls in a valid cell; the loss
+ * of a frame is the sum of squared residuals).
+ *   points_dev   n_frames x n_max float4 (x, y, z, unused), camera frame,
+ *                metres, 16-byte aligned; frame f uses its first
+ *                counts_dev[f] rows (counts_dev NULL: all n_max).
+ *   poses_dev    n_frames x 16 double, camera-to-world, row-major.
+ *   xi_dev       n_frames x 6 double (omega, v) or NULL (zero): frame f is
+ *                evaluated at q = Exp(omega) (R x + t) + v (a perturbation on
+ *                the left; Exp = Rodrigues).
+ *   dloss_dev    n_frames double or NULL (ones): upstream gradient of each
+ *                frame's loss, scaling the derivatives below.
+ *   loss_dev     out, n_frames double: sum of squared residuals.
+ *   count_dev    out, n_frames int or NULL: points in valid cells.
+ *   grad_xi_dev  out, n_frames x 6 double or NULL: dloss_f * dL_f / dxi_f
+ *                at xi_f (rotation part through the left Jacobian of SO(3)).
+ *   grad_tsdf_dev out, n_nodes float or NULL: sum_f dloss_f dL_f/dV, the
+ *                derivative with respect to the stored (tau-normalised) node
+ *                values at fixed cell validity; accumulated in 2^-40 fixed
+ *                point, so it is independent of execution order.
+ * Geometry and sums are FP64.  The first call allocates library scratch
+ * (n_frames x 2368 doubles; with grad_tsdf_dev also n_nodes x 8 bytes) kept
+ * until the volume is destroyed.  Asynchronous on cuda_stream. */
+PF_API pf_status pf_align_loss(const pf_volume* vol, const float* points_dev, const int* counts_dev, int n_max,
+                               int n_frames, const double* poses_dev, const double* xi_dev, const double* dloss_dev,
+                               double* loss_dev, int* count_dev, double* grad_xi_dev, float* grad_tsdf_dev,
+                               void* cuda_stream);
+
+/* Gradient polish of a pose after the search (a refinement of Sec. III-B's
+ * result on the same residuals): damped Gauss-Newton (Levenberg-Marquardt)
+ * on r_j = tsdf(T x_j) over the points in valid cells, with Jacobian
+ * J_j = grad r^T [-[q]x | I] for a left perturbation.  Each step solves
+ * (H + lambda diag(H)) d = -b (H = sum J^T J, b = sum J^T r) and tries the
+ * candidate [Exp(d_omega) | d_v] T; it is accepted only when it lowers the
+ * mean squared residual (then lambda /= 10), otherwise dropped
+ * (lambda *= 10); lambda starts at 1e-3.
+ *   points_dev   n_max float4 (camera frame, metres), 16-byte aligned; the
+ *                first *n_dev rows are used (n_dev NULL: all n_max), e.g.
+ *                the output of pf_backproject.
+ *   pose_dev     in/out, double[16] on the device.
+ *   steps        candidates to try (0..1000).
+ *   trace_dev    out, steps + 1 doubles or NULL: the objective before the
+ *                first step and after each step.
+ *   accepted_dev out, int or NULL: accepted steps.
+ * All state stays on the device (no synchronisation; capturable once the
+ * scratch exists -- the first call allocates it). */
+PF_API pf_status pf_polish(const pf_volume* vol, const float* points_dev, const int* n_dev, int n_max,
+                           double* pose_dev, int steps, double* trace_dev, int* accepted_dev, void* cuda_stream);
+
 /* Fitness kernel variant used by pf_fitness and the search of this volume,
  * variant = layout + 4 * mapping (0 is the default everywhere).
  *   layout  0: the cell view when the volume has one, else 2;

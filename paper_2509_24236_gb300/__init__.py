@@ -64,7 +64,7 @@ class pf_track_stats(C.Structure):
 EXPORTS = ["pf_create_volume", "pf_destroy_volume", "pf_reset_volume", "pf_volume_upload", "pf_volume_download",
            "pf_integrate", "pf_integrate_async", "pf_pose_compose", "pf_backproject", "pf_fitness", "pf_fitness_noalloc", "pf_track_frame", "pf_track_frame_async",
            "pf_track_reserve", "pf_raycast", "pf_set_fitness_variant", "pf_status_string", "pf_launch_count",
-           "pf_set_kernel_timing", "pf_kernel_timing"]
+           "pf_set_kernel_timing", "pf_kernel_timing", "pf_align_loss", "pf_polish"]
 
 _lib = None
 
@@ -109,6 +109,8 @@ def load(path: str = LIB_PATH):
         "pf_launch_count": (C.c_ulonglong, []),
         "pf_set_kernel_timing": (st, [C.c_int]),
         "pf_kernel_timing": (st, [C.c_char_p, dp, C.POINTER(C.c_longlong)]),
+        "pf_align_loss": (st, [vp, vp, vp, C.c_int, C.c_int, vp, vp, vp, vp, vp, vp, vp, vp]),
+        "pf_polish": (st, [vp, vp, vp, C.c_int, vp, C.c_int, vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -226,6 +228,25 @@ def pf_fitness(vol, points, n: int, poses, k: int, fitness, count, stream=None) 
     return _check(load().pf_fitness(vol, _dptr(points, torch.float32) if n > 0 else None, n,
                                     _dptr(poses, torch.float32), k, _dptr(fitness, torch.float32),
                                     _dptr(count, torch.int32), _stream(stream)), "pf_fitness")
+
+
+def pf_align_loss(vol, points, counts, n_max: int, n_frames: int, poses, xi, dloss, loss, count, grad_xi,
+                  grad_tsdf, stream=None) -> int:
+    import torch
+    return _check(load().pf_align_loss(vol, _dptr(points, torch.float32) if n_max > 0 else None,
+                                       _dptr(counts, torch.int32), n_max, n_frames, _dptr(poses, torch.float64),
+                                       _dptr(xi, torch.float64), _dptr(dloss, torch.float64),
+                                       _dptr(loss, torch.float64), _dptr(count, torch.int32),
+                                       _dptr(grad_xi, torch.float64), _dptr(grad_tsdf, torch.float32),
+                                       _stream(stream)), "pf_align_loss")
+
+
+def pf_polish(vol, points, n_dev, n_max: int, pose, steps: int, trace=None, accepted=None, stream=None) -> int:
+    import torch
+    return _check(load().pf_polish(vol, _dptr(points, torch.float32) if n_max > 0 else None,
+                                   _dptr(n_dev, torch.int32), n_max, _dptr(pose, torch.float64), int(steps),
+                                   _dptr(trace, torch.float64), _dptr(accepted, torch.int32), _stream(stream)),
+                  "pf_polish")
 
 
 PF_NOALLOC_MAX_SLOTS = 65536
@@ -369,6 +390,30 @@ class Volume:
     def set_fitness_variant(self, variant: int):
         pf_set_fitness_variant(self.handle, variant)
 
+    def align_loss(self, points, poses, counts=None, xi=None, dloss=None, grad_xi=False, grad_tsdf=False,
+                   stream=None):
+        """points: (F, N, 4) float32 CUDA; poses: (F, 4, 4) float64 CUDA ->
+        (loss (F,) float64, count (F,) int32, dL/dxi (F, 6) or None,
+        dL/dV (n_nodes,) float32 or None)."""
+        import torch
+        F, N = points.shape[0], points.shape[1]
+        dev = points.device
+        loss = torch.empty(F, dtype=torch.float64, device=dev)
+        cnt = torch.empty(F, dtype=torch.int32, device=dev)
+        gx = torch.empty((F, 6), dtype=torch.float64, device=dev) if grad_xi else None
+        gv = torch.empty(self.n_nodes, dtype=torch.float32, device=dev) if grad_tsdf else None
+        pf_align_loss(self.handle, points, counts, N, F, poses, xi, dloss, loss, cnt, gx, gv, stream)
+        return loss, cnt, gx, gv
+
+    def polish(self, points, pose, steps=10, n_dev=None, stream=None):
+        """Gauss-Newton polish of pose (16 float64 CUDA, in place) over
+        points (N, 4) -> (trace (steps+1,) float64, accepted (1,) int32)."""
+        import torch
+        trace = torch.empty(steps + 1, dtype=torch.float64, device=pose.device)
+        acc = torch.empty(1, dtype=torch.int32, device=pose.device)
+        pf_polish(self.handle, points, n_dev, points.shape[0], pose, steps, trace, acc, stream)
+        return trace, acc
+
     def fitness(self, points, poses, stream=None):
         """points: (N, 4) float32 CUDA; poses: (K, 12) float32 CUDA -> (E, C) CUDA tensors."""
         import torch
@@ -397,3 +442,42 @@ def backproject(depth, intr, stream=None):
     n = torch.zeros(1, dtype=torch.int32, device=depth.device)
     pf_backproject(depth, intr, pts, n, stream)
     return pts, n
+
+
+# ---------------------------------------------------------------------------
+# autograd
+# ---------------------------------------------------------------------------
+
+def _align_function():
+    import torch
+
+    class AlignLoss(torch.autograd.Function):
+        """L_f = sum of squared TSDF residuals of frame f at pose
+        Exp(omega_f) (R_f x + t_f) + v_f; differentiable in xi = (omega, v)
+        and, through `tsdf_sink`, in the volume's stored node values (the
+        sink's values are not read; its gradient receives dL/dV)."""
+
+        @staticmethod
+        def forward(ctx, xi, tsdf_sink, vol, points, poses, counts):
+            loss, cnt, _, _ = vol.align_loss(points, poses, counts=counts, xi=xi.detach().contiguous())
+            ctx.vol, ctx.points, ctx.poses, ctx.counts = vol, points, poses, counts
+            ctx.save_for_backward(xi)
+            ctx.want_v = tsdf_sink is not None and tsdf_sink.requires_grad
+            return loss
+
+        @staticmethod
+        def backward(ctx, dloss):
+            (xi,) = ctx.saved_tensors
+            _, _, gx, gv = ctx.vol.align_loss(ctx.points, ctx.poses, counts=ctx.counts,
+                                              xi=xi.detach().contiguous(),
+                                              dloss=dloss.detach().to(torch.float64).contiguous(),
+                                              grad_xi=ctx.needs_input_grad[0], grad_tsdf=ctx.want_v)
+            return gx, gv, None, None, None, None
+
+    return AlignLoss
+
+
+def align_loss(vol, points, poses, xi, counts=None, tsdf_sink=None):
+    """Differentiable alignment loss (see AlignLoss).  points (F, N, 4) f32,
+    poses (F, 4, 4) f64, xi (F, 6) f64 (requires_grad for dL/dxi)."""
+    return _align_function().apply(xi, tsdf_sink, vol, points, poses, counts)

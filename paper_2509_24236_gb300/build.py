@@ -22,11 +22,11 @@ INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",
               "--expt-relaxed-constexpr", "-I", INCLUDE]
-# Per-file flags.  track.cu: no automatic multiply-add contraction, so every
-# fused multiply-add is one written in the source and every instantiation of
-# the fitness kernel rounds the same way (the error-free products of the
-# reference transform rely on separately rounded products and sums).
-FILE_FLAGS = {"track.cu": ["--fmad=false"]}
+# Per-file flags.  track.cu, align.cu: no automatic multiply-add
+# contraction, so every fused multiply-add is one written in the source and
+# every kernel instantiation rounds the same way (the error-free products of
+# the reference transform rely on separately rounded products and sums).
+FILE_FLAGS = {"track.cu": ["--fmad=false"], "align.cu": ["--fmad=false"]}
 
 
 def nvcc() -> str:

@@ -23,6 +23,10 @@
 
 #include "pf_internal.cuh"
 
+namespace pf {
+void align_release(const pf_volume* v);  // align.cu
+}
+
 namespace {
 
 constexpr int TX = PF_TX, TY = PF_TY, TZ = PF_TZ;
@@ -348,6 +352,7 @@ pf_status pf_destroy_volume(pf_volume* v)
 {
     if (!v) return PF_OK;
     cudaDeviceSynchronize();
+    pf::align_release(v);
     cudaFree(v->tsdf);
     cudaFree(v->weight);
     cudaFree(v->cells);

@@ -80,6 +80,9 @@ def test_host_side_validation_without_a_gpu(lib):
     assert lib.pf_fitness(None, None, 0, None, 1, None, None, None) == pf.PF_ERR_INVALID_ARG
     assert lib.pf_raycast(None, C.byref(intr), pose, None, None, None) == pf.PF_ERR_INVALID_ARG
     assert lib.pf_track_frame(None, None, C.byref(intr), None, pose, pose, None, None) == pf.PF_ERR_INVALID_ARG
+    assert lib.pf_align_loss(None, None, None, 0, 1, None, None, None, None, None, None, None,
+                             None) == pf.PF_ERR_INVALID_ARG
+    assert lib.pf_polish(None, None, None, 0, None, 10, None, None, None) == pf.PF_ERR_INVALID_ARG
     bad_intr = pf.pf_intrinsics(0, 3, 2.0, 2.0, 1.5, 1.0, 0.1, 8.0)
     assert lib.pf_backproject(C.c_void_p(1), C.byref(bad_intr), C.c_void_p(1), 100, C.c_void_p(1),
                               None) == pf.PF_ERR_INVALID_ARG
