@@ -60,10 +60,11 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ref-particles", type=int, default=192,
                     help="particles per reference-arm step (a bounded slice of one iteration)")
-    ap.add_argument("--kernel", default=None, choices=["fitness", "integrate", "align"],
+    ap.add_argument("--kernel", default=None, choices=["fitness", "integrate", "align", "batch"],
                     help="time one kernel on the multiroom volume instead of the frame loop (profiling); "
                          "align: loss + pose and node gradients of 64 320x240 frames against a 256^3 volume, "
-                         "and the 10-step polish")
+                         "and the 10-step polish; batch: 32 sequences of mixed camera and volume size stepped "
+                         "together (pf_batch, CUDA graph) against the same sequences one after another")
     ap.add_argument("--spread", type=float, default=3.0,
                     help="--kernel fitness: poses perturbed up to this many degrees and centimetres")
     ap.add_argument("--reps", type=int, default=3, help="--kernel: timed launches after one warm-up launch")
@@ -649,8 +650,148 @@ def run_align(args):
     return 0
 
 
+BATCH_SEQS = 32
+BATCH_RES = [(160, 120), (320, 240), (640, 480)]
+BATCH_GRIDS = [128, 256, 384]          # nodes per axis over the 5.12 m multiroom cube (4, 2, 1.33 cm)
+BATCH_K = [1024, 2048, 3072, 4096]
+
+
+def batch_sequence(res: int, grid: int, seed: int):
+    import synth
+    w, h = BATCH_RES[res]
+    f = 525.0 * w / 640.0
+    intr = synth.Intrinsics(w, h, f, f, (w - 1) / 2.0, (h - 1) / 2.0, 0.1, 8.0)
+    vs = 5.12 / BATCH_GRIDS[grid]
+    g = synth.Grid(BATCH_GRIDS[grid], BATCH_GRIDS[grid], BATCH_GRIDS[grid], vs, 3.0 * vs, (0.0, 0.0, 0.0))
+    return synth.multiroom_sequence(300, seed, grid=g, intr=intr)
+
+
+def _render_batch(args):
+    res, f, seed = args
+    return batch_sequence(res, 0, seed).depth(f)
+
+
+def run_batch(args):
+    """C4-style batch: 32 sequences, camera i % 3 of 160x120 / 320x240 /
+    640x480, volume (i // 3) % 3 of 128^3 / 256^3 / 384^3 over the same
+    5.12 m scene, K = 1024 / 2048 / 3072 / 4096 by i % 4, 20 iterations over
+    all points.  Frames 1..W+S of the multiroom trajectory (one rendering per
+    camera size, shared by the sequences of that size); frame 0 is fused at
+    its true pose.  Times S steps of all sequences (a) one sequence after
+    another with pf_track_frame_async + pf_integrate_async, (b) as a batch
+    with direct launches, (c) as a batch replaying a CUDA graph.  Inputs are
+    resident on the device.  Prints one JSON line (aggregate frames/s)."""
+    import multiprocessing as mp
+    W, S = max(1, args.warmup), max(1, args.steps)
+    n_frames = 1 + W + S
+    jobs = [(r, f, args.seed) for r in range(len(BATCH_RES)) for f in range(n_frames)]
+    with mp.get_context("spawn").Pool(max(1, min(16, (os.cpu_count() or 2) - 1))) as pool:
+        rendered = pool.map(_render_batch, jobs)
+    import torch
+
+    import paper_2509_24236_gb300 as pf
+    import synth
+    from paper_2509_24236_gb300 import build as pfbuild
+    pfbuild.build()
+    pf.load()
+    dev = torch.device("cuda", 0)
+    depth = {}
+    for (r, f, _), d in zip(jobs, rendered):
+        depth[r, f] = torch.from_numpy(d).to(dev)
+    seqs, vols, params = [], [], []
+    templ = torch.from_numpy(synth.templates(max(BATCH_K), args.seed)).to(dev)
+    for i in range(BATCH_SEQS):
+        r, g, K = i % 3, (i // 3) % 3, BATCH_K[i % 4]
+        seq = batch_sequence(r, g, args.seed + i)
+        seqs.append((r, seq))
+        vols.append(new_volume(pf, seq.grid, args))
+        params.append(pf.track_params(templ, n_iters=N_ITERS, k_sched=(K, K, K), decim_sched=(1, 1, 1),
+                                      update_mode=args.update_mode, compose_mode=args.compose_mode,
+                                      min_valid_frac=0.05))
+    rels = [torch.from_numpy(np.stack([seq.relative_init(f).reshape(16) if f else np.eye(4).reshape(16)
+                                       for f in range(n_frames)])).to(dev) for _, seq in seqs]
+
+    def timed(run_steps):
+        torch.cuda.synchronize()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record()
+        run_steps()
+        b.record()
+        torch.cuda.synchronize()
+        return a.elapsed_time(b)
+
+    # (a) one sequence after another
+    for v in vols:
+        v.reserve(640 * 480, max(BATCH_K))
+    pose = torch.zeros((BATCH_SEQS, n_frames, 16), dtype=torch.float64, device=dev)
+    init = torch.zeros_like(pose)
+    for i, (r, seq) in enumerate(seqs):
+        pose[i, 0] = torch.from_numpy(seq.gt[0].reshape(16)).to(dev)
+        vols[i].integrate_async(depth[r, 0], seq.intr, pose[i, 0])
+
+    def seq_frames(f0, f1):
+        for f in range(f0, f1):
+            for i, (r, seq) in enumerate(seqs):
+                pf.pf_pose_compose(pose[i, f - 1], rels[i][f], init[i, f])
+                vols[i].track_frame_async(depth[r, f], seq.intr, params[i], init[i, f], pose[i, f])
+                vols[i].integrate_async(depth[r, f], seq.intr, pose[i, f])
+
+    seq_frames(1, W + 1)
+    ms_seq = timed(lambda: seq_frames(W + 1, W + S + 1))
+    pose_seq = pose.cpu().numpy()
+
+    # (b), (c) batches, from the same start
+    out = {}
+    for use_graph in (False, True):
+        for v in vols:
+            v.reset()
+        batch = pf.Batch(vols, [seq.intr for _, seq in seqs], params, use_graph=use_graph)
+        for i, (r, seq) in enumerate(seqs):
+            batch.pose[i].copy_(torch.from_numpy(seq.gt[0]).to(dev))
+            batch.depth[i].copy_(depth[r, 0])
+        batch.fuse()
+
+        def load(f):
+            for i, (r, seq) in enumerate(seqs):
+                batch.depth[i].copy_(depth[r, f])
+                batch.rel[i].copy_(rels[i][f].reshape(4, 4))
+
+        if use_graph:
+            load(1)
+            out["points_per_block"] = batch.autotune()
+        for f in range(1, W + 1):
+            load(f)
+            batch.step()
+        times = []
+        for f in range(W + 1, W + S + 1):
+            load(f)  # input copies stay outside the timed region
+            times.append(timed(batch.step))
+        out["graph" if use_graph else "direct"] = sum(times)
+        poses_b = np.stack([batch.pose[i].cpu().numpy().reshape(16) for i in range(BATCH_SEQS)])
+        out["pose_diff_m"] = float(np.max(np.abs(poses_b[:, 3::4][:, :3] - pose_seq[:, W + S, 3::4][:, :3])))
+        batch.close()
+    frames = BATCH_SEQS * S
+    print(json.dumps({
+        "kernel": "batch", "sequences": BATCH_SEQS, "steps": S, "warmup": W, "storage": storage_desc(args),
+        "mix": "cameras 160x120/320x240/640x480 by i%3, volumes 128^3/256^3/384^3 over 5.12 m by (i//3)%3, "
+               "K 1024/2048/3072/4096 by i%4, 20 iterations, all points",
+        "frames_per_s_sequential": frames / (ms_seq / 1e3),
+        "frames_per_s_batch_direct": frames / (out["direct"] / 1e3),
+        "frames_per_s_batch_graph": frames / (out["graph"] / 1e3),
+        "speedup_graph_vs_sequential": ms_seq / out["graph"],
+        "points_per_block": out.get("points_per_block"),
+        "max_final_position_difference_batch_vs_sequential_m": out["pose_diff_m"],
+    }))
+    for v in vols:
+        v.close()
+    return 0
+
+
 def main():
     args = parse()
+    if args.kernel == "batch":
+        return run_batch(args)
     if args.kernel == "align":
         return run_align(args)
     if args.kernel:

@@ -260,6 +260,48 @@ PF_API pf_status pf_track_reserve(pf_volume* vol, int max_pixels, int k_max);
 PF_API pf_status pf_raycast(const pf_volume* vol, const pf_intrinsics* intr, const double cam_to_world[16],
                      float* depth_out_dev, float* normal_out_dev_or_null, void* cuda_stream);
 
+/* ---------------------------------------------------------------------------
+ * Batches: many independent sequences (each with its own volume, camera and
+ * search parameters; sizes may differ) stepped together.  One step is one
+ * frame of every sequence: the initial pose is the sequence's current pose
+ * times its relative pose input (P_t^(0) = P_{t-1} P_(t,t-1), Sec. III-A),
+ * the randomized optimization of Sec. III-B runs from it, and the frame is
+ * fused at the result (Sec. III).  Each search iteration of all sequences is
+ * one launch over the thread blocks of every sequence (each sequence keeps
+ * its own arguments, partial sums and selection, so its results equal those
+ * of pf_track_frame_async with the same point tiling), and with use_graph
+ * the whole step is captured once as a CUDA graph and replayed.
+ *   vols     n distinct volumes (a volume holds one sequence's search state),
+ *            all with the same tsdf storage type and fitness layout (the
+ *            plain layout is not supported); their workspaces are reserved
+ *            here.  The batch does not own them; destroy it first.
+ *   intrs, params  n entries each (templates stay owned by the caller).
+ * Buffers owned by the batch, on the device (pf_batch_buffers): per sequence
+ * the depth image (width x height float, written by the caller before each
+ * step), the relative pose input and the current pose (double[16] each; the
+ * current pose starts as the identity -- write the first frame's pose
+ * there) and the search record of the last step.
+ * pf_batch_fuse fuses every sequence's depth at its current pose (the first
+ * frame).  pf_batch_step enqueues one step on cuda_stream (the first step
+ * with use_graph captures the graph on a private stream; later steps replay
+ * it; nothing synchronises).  pf_batch_autotune picks the evaluated points
+ * per thread block of the batched launches by timing the first search
+ * iteration of the current frames (on copies of the search state, at the
+ * initial and at a contracted search size); it synchronises and drops any
+ * captured graph.  pf_batch_set_points_per_block sets that value directly
+ * (>= 1024).  Errors: PF_ERR_INVALID_ARG for bad arguments (before any
+ * allocation), PF_ERR_UNSUPPORTED for mixed storage types or layouts. */
+typedef struct pf_batch pf_batch;
+PF_API pf_status pf_batch_create(int n, pf_volume* const* vols, const pf_intrinsics* intrs,
+                                 const pf_track_params* params, int use_graph, pf_batch** out);
+PF_API pf_status pf_batch_destroy(pf_batch* batch);
+PF_API pf_status pf_batch_buffers(pf_batch* batch, int i, float** depth_dev, double** rel_pose_dev,
+                                  double** pose_dev, pf_track_stats** stats_dev);
+PF_API pf_status pf_batch_fuse(pf_batch* batch, void* cuda_stream);
+PF_API pf_status pf_batch_step(pf_batch* batch, void* cuda_stream);
+PF_API pf_status pf_batch_autotune(pf_batch* batch, void* cuda_stream, int* points_per_block_out);
+PF_API pf_status pf_batch_set_points_per_block(pf_batch* batch, int points_per_block);
+
 /* Alignment loss of n_frames poses against their frames' points, and its
  * derivatives -- the gradient counterpart of the fitness (Sec. III-B: the
  * residual of a point is the TSDF at the transformed point, normalised by

@@ -64,7 +64,9 @@ class pf_track_stats(C.Structure):
 EXPORTS = ["pf_create_volume", "pf_destroy_volume", "pf_reset_volume", "pf_volume_upload", "pf_volume_download",
            "pf_integrate", "pf_integrate_async", "pf_pose_compose", "pf_backproject", "pf_fitness", "pf_fitness_noalloc", "pf_track_frame", "pf_track_frame_async",
            "pf_track_reserve", "pf_raycast", "pf_set_fitness_variant", "pf_status_string", "pf_launch_count",
-           "pf_set_kernel_timing", "pf_kernel_timing", "pf_align_loss", "pf_polish"]
+           "pf_set_kernel_timing", "pf_kernel_timing", "pf_align_loss", "pf_polish",
+           "pf_batch_create", "pf_batch_destroy", "pf_batch_buffers", "pf_batch_fuse", "pf_batch_step",
+           "pf_batch_autotune", "pf_batch_set_points_per_block"]
 
 _lib = None
 
@@ -111,6 +113,14 @@ def load(path: str = LIB_PATH):
         "pf_kernel_timing": (st, [C.c_char_p, dp, C.POINTER(C.c_longlong)]),
         "pf_align_loss": (st, [vp, vp, vp, C.c_int, C.c_int, vp, vp, vp, vp, vp, vp, vp, vp]),
         "pf_polish": (st, [vp, vp, vp, C.c_int, vp, C.c_int, vp, vp, vp]),
+        "pf_batch_create": (st, [C.c_int, C.POINTER(vp), C.POINTER(pf_intrinsics), C.POINTER(pf_track_params),
+                                 C.c_int, C.POINTER(vp)]),
+        "pf_batch_destroy": (st, [vp]),
+        "pf_batch_buffers": (st, [vp, C.c_int, C.POINTER(vp), C.POINTER(vp), C.POINTER(vp), C.POINTER(vp)]),
+        "pf_batch_fuse": (st, [vp, vp]),
+        "pf_batch_step": (st, [vp, vp]),
+        "pf_batch_autotune": (st, [vp, vp, C.POINTER(C.c_int)]),
+        "pf_batch_set_points_per_block": (st, [vp, C.c_int]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -481,3 +491,72 @@ def align_loss(vol, points, poses, xi, counts=None, tsdf_sink=None):
     """Differentiable alignment loss (see AlignLoss).  points (F, N, 4) f32,
     poses (F, 4, 4) f64, xi (F, 6) f64 (requires_grad for dL/dxi)."""
     return _align_function().apply(xi, tsdf_sink, vol, points, poses, counts)
+
+
+# ---------------------------------------------------------------------------
+# batches of sequences
+# ---------------------------------------------------------------------------
+
+class _DevArray:
+    """A view of library-owned device memory for torch.as_tensor."""
+
+    def __init__(self, ptr: int, shape, typestr: str):
+        self.__cuda_array_interface__ = {"shape": tuple(shape), "typestr": typestr, "data": (ptr, False),
+                                         "version": 3, "strides": None}
+
+
+class Batch:
+    """Independent sequences stepped together (pf_batch_*).  The depth,
+    relative-pose, pose and stats buffers are library-owned device memory,
+    exposed as torch tensors that alias it."""
+
+    def __init__(self, volumes, cams, params, use_graph=True):
+        import torch
+        n = len(volumes)
+        self._volumes = list(volumes)   # keep the volumes alive
+        self._params = list(params)     # and the templates their params point to
+        vols = (C.c_void_p * n)(*[v.handle for v in volumes])
+        intrs = (pf_intrinsics * n)(*[intrinsics(c) for c in cams])
+        prms = (pf_track_params * n)(*params)
+        out = C.c_void_p()
+        _check(load().pf_batch_create(n, vols, intrs, prms, int(bool(use_graph)), C.byref(out)), "pf_batch_create")
+        self.handle = out
+        self.n = n
+        self.depth, self.rel, self.pose, self.stats = [], [], [], []
+        sz = C.sizeof(pf_track_stats)
+        for i, intr in enumerate(cams):
+            d, r, p, st = C.c_void_p(), C.c_void_p(), C.c_void_p(), C.c_void_p()
+            _check(load().pf_batch_buffers(out, i, C.byref(d), C.byref(r), C.byref(p), C.byref(st)),
+                   "pf_batch_buffers")
+            self.depth.append(torch.as_tensor(_DevArray(d.value, (intr.height, intr.width), "<f4"), device="cuda"))
+            self.rel.append(torch.as_tensor(_DevArray(r.value, (4, 4), "<f8"), device="cuda"))
+            self.pose.append(torch.as_tensor(_DevArray(p.value, (4, 4), "<f8"), device="cuda"))
+            self.stats.append(torch.as_tensor(_DevArray(st.value, (sz,), "|u1"), device="cuda"))
+
+    def fuse(self, stream=None):
+        _check(load().pf_batch_fuse(self.handle, _stream(stream)), "pf_batch_fuse")
+
+    def step(self, stream=None):
+        _check(load().pf_batch_step(self.handle, _stream(stream)), "pf_batch_step")
+
+    def autotune(self, stream=None) -> int:
+        c = C.c_int()
+        _check(load().pf_batch_autotune(self.handle, _stream(stream), C.byref(c)), "pf_batch_autotune")
+        return c.value
+
+    def set_points_per_block(self, p: int):
+        _check(load().pf_batch_set_points_per_block(self.handle, int(p)), "pf_batch_set_points_per_block")
+
+    def stats_dict(self, i: int) -> dict:
+        return pf_track_stats.from_buffer_copy(self.stats[i].cpu().numpy().tobytes()).to_dict()
+
+    def close(self):
+        if getattr(self, "handle", None):
+            load().pf_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -66,6 +66,17 @@ void timing_end(KernelClass kc, cudaStream_t s)
     t.is_open[kc] = false;
 }
 
+// Sets whether launches are timed; returns the previous setting (used to
+// keep event records out of captured graphs).
+bool timing_swap(bool enabled)
+{
+    TimingState& t = timing();
+    std::lock_guard<std::mutex> lock(t.mu);
+    const bool was = t.enabled;
+    t.enabled = enabled;
+    return was;
+}
+
 pf_status check_intrinsics(const pf_intrinsics* in)
 {
     if (!in) return PF_ERR_INVALID_ARG;

@@ -41,6 +41,7 @@
 #include <algorithm>
 #include <climits>
 #include <mutex>
+#include <vector>
 
 #include "pf_internal.cuh"
 
@@ -692,8 +693,11 @@ __device__ inline void argmin_pair(float& e, int& k, float* se, int* sk)
 #define PF_FIT_MIN_BLOCKS 3
 #endif
 
+// The work of one CTA: particle chunk bx, point tile by, of a launch of
+// n_blocks CTAs for this problem (the last of them to finish runs the
+// epilogue).
 template <int SRC, int VARIANT, typename TS>
-__global__ void __launch_bounds__(FIT_THREADS, PF_FIT_MIN_BLOCKS) fitness_kernel(FitArgs a)
+__device__ __forceinline__ void fitness_body(const FitArgs& a, int bx, int by, unsigned n_blocks)
 {
     __shared__ Particle sP[KC];
     __shared__ ParticleD sPD[KC];
@@ -715,7 +719,7 @@ __global__ void __launch_bounds__(FIT_THREADS, PF_FIT_MIN_BLOCKS) fitness_kernel
     __shared__ int s_lo[3], s_hi[3];
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int k_begin = blockIdx.x * KC;
+    const int k_begin = bx * KC;
     const int kc = min(KC, a.K - k_begin);
     const int nx = a.nx, nxy = a.nx * a.ny;
     const unsigned mx = a.nx - 1, my = a.ny - 1, mz = a.nz - 1;
@@ -781,8 +785,8 @@ __global__ void __launch_bounds__(FIT_THREADS, PF_FIT_MIN_BLOCKS) fitness_kernel
 
     const int N = a.n_dev ? *a.n_dev : a.n_host;
     const long long Ne = N > 0 ? ((long long)N + a.stride - 1) / a.stride : 0;
-    const long long beg = Ne * blockIdx.y / a.n_ptiles;
-    const long long end = Ne * (blockIdx.y + 1) / a.n_ptiles;
+    const long long beg = Ne * by / a.n_ptiles;
+    const long long end = Ne * (by + 1) / a.n_ptiles;
 
     if (!skip) {
         for (long long sub = beg; sub < end; sub += SUBTILE) {
@@ -961,7 +965,7 @@ __global__ void __launch_bounds__(FIT_THREADS, PF_FIT_MIN_BLOCKS) fitness_kernel
             S += accS[w][tid];
             C += accC[w][tid];
         }
-        const size_t slot = (size_t)blockIdx.y * a.K + k_begin + tid;
+        const size_t slot = (size_t)by * a.K + k_begin + tid;
         a.part_S[slot] = S;
         a.part_C[slot] = C;
     }
@@ -969,7 +973,7 @@ __global__ void __launch_bounds__(FIT_THREADS, PF_FIT_MIN_BLOCKS) fitness_kernel
     __syncthreads();
     if (tid == 0) {
         const unsigned int ticket = atomicAdd(a.counter, 1u);
-        s_last = ticket == gridDim.x * gridDim.y - 1;
+        s_last = ticket == n_blocks - 1;
     }
     __syncthreads();
     if (!s_last) return;
@@ -1129,6 +1133,45 @@ __global__ void __launch_bounds__(FIT_THREADS, PF_FIT_MIN_BLOCKS) fitness_kernel
         }
     }
     if (tid == 0) *a.counter = 0u;
+}
+
+template <int SRC, int VARIANT, typename TS>
+__global__ void __launch_bounds__(FIT_THREADS, PF_FIT_MIN_BLOCKS) fitness_kernel(FitArgs a)
+{
+    fitness_body<SRC, VARIANT, TS>(a, blockIdx.x, blockIdx.y, gridDim.x * gridDim.y);
+}
+
+// One launch over the CTAs of several independent problems (the sequences
+// of a batch): problem i owns CTAs [first[i], first[i + 1]), chunk-fastest,
+// with its own arguments, partials, ticket counter and epilogue, so each
+// problem's results are those of its own launch.
+template <int SRC, int VARIANT, typename TS>
+__global__ void __launch_bounds__(FIT_THREADS, PF_FIT_MIN_BLOCKS)
+    fitness_kernel_batch(const FitArgs* __restrict__ args, const int* __restrict__ first, int n)
+{
+    __shared__ FitArgs sa;
+    __shared__ int s_id;
+    if (threadIdx.x == 0) {
+        int lo = 0, hi = n - 1;  // the last problem with first[i] <= blockIdx.x
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (first[mid] <= (int)blockIdx.x)
+                lo = mid;
+            else
+                hi = mid - 1;
+        }
+        s_id = lo;
+    }
+    __syncthreads();
+    const int id = s_id;
+    static_assert(sizeof(FitArgs) % 4 == 0, "FitArgs is copied as words");
+    const int* src = reinterpret_cast<const int*>(args + id);
+    int* dst = reinterpret_cast<int*>(&sa);
+    for (int q = threadIdx.x; q < (int)(sizeof(FitArgs) / 4); q += FIT_THREADS) dst[q] = __ldg(src + q);
+    __syncthreads();
+    const int local = (int)blockIdx.x - __ldg(first + id);
+    const int chunks = (sa.K + KC - 1) / KC;
+    fitness_body<SRC, VARIANT, TS>(sa, local % chunks, local / chunks, (unsigned)(chunks * sa.n_ptiles));
 }
 
 __global__ void track_begin_kernel(SearchState* st, const double* P0, double s_deg, double s_cm,
@@ -1488,6 +1531,442 @@ pf_status pf_track_frame(pf_volume* v, const float* depth_dev, const pf_intrinsi
 // fixed array below, which every device that loads the library holds until
 // the process exits.
 // ---------------------------------------------------------------------------
+// ---------------------------------------------------------------------------
+// Batches: many independent sequences stepped together
+// ---------------------------------------------------------------------------
+namespace pf {
+bool timing_swap(bool enabled);  // api.cu
+}
+
+struct pf_batch {
+    int n = 0;
+    std::vector<pf_volume*> vols;
+    std::vector<pf_intrinsics> intrs;
+    std::vector<pf_track_params> params;
+    int max_iters = 0;
+    int layout = 3;
+    pf_dtype dtype = PF_F32;
+    int device = 0;
+    // device buffers: depth images (one allocation), per sequence four poses
+    // (relative input, current pose, initial pose of the search, spare) and
+    // the search record
+    float* depth = nullptr;
+    std::vector<size_t> depth_off;
+    double* poses = nullptr;
+    pf_track_stats* stats = nullptr;
+    // launch tables, per iteration: arguments of every participating
+    // sequence and the first CTA of each (search, then single-pose
+    // evaluation for the mean update)
+    FitArgs* d_args = nullptr;
+    int* d_first = nullptr;
+    std::vector<int> n_search, blocks_search, n_eval, blocks_eval;
+    int points_per_block = 4096;
+    // graph
+    bool use_graph = false;
+    cudaStream_t cap = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    unsigned long long launches_per_step = 0;
+    // autotuner scratch: search states and records
+    SearchState* tune_state = nullptr;
+    pf_track_stats* tune_stats = nullptr;
+
+    double* rel(int i) const { return poses + 64 * (size_t)i; }
+    double* pose(int i) const { return poses + 64 * (size_t)i + 16; }
+    double* init(int i) const { return poses + 64 * (size_t)i + 32; }
+};
+
+namespace {
+
+int resolve_layout(const pf_volume* v)
+{
+    const int layout = v->fitness_variant & 3;
+    return layout == 0 ? (v->cells ? 3 : 2) : layout;
+}
+
+float mapping_threshold(const pf_volume* v, int layout)
+{
+    const int mapping = (v->fitness_variant >> 2) & 3;
+    return mapping == 1 ? -1.0f : mapping == 2 ? INFINITY
+                                               : (layout == 3 ? kParticleLanesBelowCells : kParticleLanesBelowNodes);
+}
+
+// Point tiles of one problem in a batched launch: about points_per_block
+// evaluated points per CTA (work per CTA alike across problems of unequal
+// size); a single-pose evaluation spreads over up to 8 CTAs per SM.
+int batch_tiles(const pf_batch* b, int K, long long ne_max)
+{
+    const long long max_tiles = std::max(1LL, (ne_max + SUBTILE - 1) / SUBTILE);
+    long long t = K == 1 ? (long long)device_sms(b->device) * 8 : (ne_max + b->points_per_block - 1) / b->points_per_block;
+    return (int)std::max(1LL, std::min(t, max_tiles));
+}
+
+FitArgs batch_args(const pf_batch* b, int i, SearchState* st, pf_track_stats* stats)
+{
+    const pf_volume* v = b->vols[i];
+    const pf_track_params& p = b->params[i];
+    FitArgs a;
+    memset(&a, 0, sizeof(a));
+    a.pts = v->ws.points;
+    a.n_dev = v->ws.n_points;
+    a.templ = p.templates_dev;
+    a.st = st;
+    a.compose_mode = p.compose_mode;
+    a.update_mode = p.update_mode;
+    a.beta = p.beta;
+    a.min_valid_frac = p.min_valid_frac;
+    fill_volume_args(a, v);
+    a.part_S = v->ws.part_S;
+    a.part_C = v->ws.part_C;
+    a.counter = v->ws.counter;
+    a.stats = stats;
+    a.pm_threshold = mapping_threshold(v, b->layout);
+    return a;
+}
+
+// Builds and uploads the launch tables.  tune: only iteration 0's search,
+// on the tuning states (used by the autotuner).
+pf_status batch_tables(pf_batch* b, bool tune)
+{
+    const int n = b->n, iters = b->max_iters;
+    // partial slots each volume needs over all iterations, grown first (a
+    // reallocation would leave stale pointers in earlier table entries)
+    for (int i = 0; i < n; ++i) {
+        const pf_track_params& p = b->params[i];
+        const long long npix = (long long)b->intrs[i].width * b->intrs[i].height;
+        size_t need = 0;
+        for (int it = 0; it < p.n_iters; ++it) {
+            const int stride = p.decim_sched[it % 3];
+            const long long ne_max = (npix + stride - 1) / stride;
+            need = std::max(need, (size_t)batch_tiles(b, p.k_sched[it % 3], ne_max) * p.k_sched[it % 3]);
+            need = std::max(need, (size_t)batch_tiles(b, 1, ne_max));
+        }
+        pf_status st = grow_partials(b->vols[i], need);
+        if (st != PF_OK) return st;
+    }
+    std::vector<FitArgs> args((size_t)iters * 2 * n);
+    std::vector<int> first((size_t)iters * 2 * (n + 1), 0);
+    b->n_search.assign(iters, 0);
+    b->blocks_search.assign(iters, 0);
+    b->n_eval.assign(iters, 0);
+    b->blocks_eval.assign(iters, 0);
+    for (int it = 0; it < iters; ++it) {
+        for (int kind = 0; kind < 2; ++kind) {
+            int cnt = 0, blocks = 0;
+            FitArgs* A = args.data() + ((size_t)it * 2 + kind) * n;
+            int* F = first.data() + ((size_t)it * 2 + kind) * (n + 1);
+            for (int i = 0; i < n; ++i) {
+                const pf_track_params& p = b->params[i];
+                if (it >= p.n_iters || (tune && (it > 0 || kind == 1))) continue;
+                if (kind == 1 && p.update_mode != 0) continue;
+                const int K = kind == 0 ? p.k_sched[it % 3] : 1;
+                const int stride = p.decim_sched[it % 3];
+                const long long npix = (long long)b->intrs[i].width * b->intrs[i].height;
+                const long long ne_max = (npix + stride - 1) / stride;
+                FitArgs a = tune ? batch_args(b, i, b->tune_state + i, b->tune_stats + i)
+                                 : batch_args(b, i, reinterpret_cast<SearchState*>(b->vols[i]->ws.state),
+                                              b->stats + i);
+                a.K = K;
+                a.stride = stride;
+                a.iter = it;
+                a.n_ptiles = batch_tiles(b, K, ne_max);
+                A[cnt] = a;
+                F[cnt] = blocks;
+                blocks += ((K + KC - 1) / KC) * a.n_ptiles;
+                ++cnt;
+            }
+            F[cnt] = blocks;
+            (kind == 0 ? b->n_search : b->n_eval)[it] = cnt;
+            (kind == 0 ? b->blocks_search : b->blocks_eval)[it] = blocks;
+        }
+    }
+    if (!b->d_args) {
+        PF_CUDA(cudaMalloc(&b->d_args, args.size() * sizeof(FitArgs)));
+        PF_CUDA(cudaMalloc(&b->d_first, first.size() * sizeof(int)));
+    }
+    PF_CUDA(cudaMemcpy(b->d_args, args.data(), args.size() * sizeof(FitArgs), cudaMemcpyHostToDevice));
+    PF_CUDA(cudaMemcpy(b->d_first, first.data(), first.size() * sizeof(int), cudaMemcpyHostToDevice));
+    return PF_OK;
+}
+
+template <int SRC, typename TS>
+void launch_batch_t(const pf_batch* b, const FitArgs* args, const int* first, int n, int blocks, cudaStream_t s)
+{
+    if (b->layout == 2)
+        fitness_kernel_batch<SRC, 0, TS><<<blocks, FIT_THREADS, 0, s>>>(args, first, n);
+    else
+        fitness_kernel_batch<SRC, 2, TS><<<blocks, FIT_THREADS, 0, s>>>(args, first, n);
+}
+
+template <int SRC>
+void launch_batch(const pf_batch* b, int it, int kind, cudaStream_t s)
+{
+    const int n = kind == 0 ? b->n_search[it] : b->n_eval[it];
+    const int blocks = kind == 0 ? b->blocks_search[it] : b->blocks_eval[it];
+    if (n == 0) return;
+    const FitArgs* args = b->d_args + ((size_t)it * 2 + kind) * b->n;
+    const int* first = b->d_first + ((size_t)it * 2 + kind) * (b->n + 1);
+    if (b->dtype == PF_F16)
+        launch_batch_t<SRC, __half>(b, args, first, n, blocks, s);
+    else if (b->dtype == PF_BF16)
+        launch_batch_t<SRC, __nv_bfloat16>(b, args, first, n, blocks, s);
+    else
+        launch_batch_t<SRC, float>(b, args, first, n, blocks, s);
+    pf::count_launch();
+}
+
+// One frame of every sequence: compose the initial pose, back-project,
+// search (one launch per iteration for all sequences), record the result,
+// fuse.
+pf_status batch_enqueue(pf_batch* b, cudaStream_t s)
+{
+    for (int i = 0; i < b->n; ++i) {
+        pf_status st = pf_pose_compose(b->pose(i), b->rel(i), b->init(i), s);
+        if (st != PF_OK) return st;
+        pf_volume* v = b->vols[i];
+        track_begin_kernel<<<1, 32, 0, s>>>(reinterpret_cast<SearchState*>(v->ws.state), b->init(i),
+                                            b->params[i].init_rot_deg, b->params[i].init_trans_cm, b->stats + i);
+        pf::count_launch();
+        st = enqueue_backproject(b->depth + b->depth_off[i], &b->intrs[i], v->ws.points, v->ws.block_counts,
+                                 v->ws.n_points, s);
+        if (st != PF_OK) return st;
+    }
+    for (int it = 0; it < b->max_iters; ++it) {
+        launch_batch<SRC_SEARCH>(b, it, 0, s);
+        launch_batch<SRC_EVAL>(b, it, 1, s);
+    }
+    PF_LAUNCHED();
+    for (int i = 0; i < b->n; ++i) {
+        pf_volume* v = b->vols[i];
+        track_end_kernel<<<1, 32, 0, s>>>(reinterpret_cast<const SearchState*>(v->ws.state), v->ws.n_points,
+                                          b->pose(i), b->stats + i);
+        pf::count_launch();
+        pf_status st = pf_integrate_async(v, b->depth + b->depth_off[i], &b->intrs[i], b->pose(i), s);
+        if (st != PF_OK) return st;
+    }
+    PF_LAUNCHED();
+    return PF_OK;
+}
+
+void batch_drop_graph(pf_batch* b)
+{
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    b->exec = nullptr;
+    b->graph = nullptr;
+}
+
+}  // namespace
+
+extern "C" {
+
+pf_status pf_batch_create(int n, pf_volume* const* vols, const pf_intrinsics* intrs, const pf_track_params* params,
+                          int use_graph, pf_batch** out)
+{
+    if (!out) return PF_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (n < 1 || n > 4096 || !vols || !intrs || !params) return PF_ERR_INVALID_ARG;
+    for (int i = 0; i < n; ++i) {
+        if (!vols[i]) return PF_ERR_INVALID_ARG;
+        for (int j = 0; j < i; ++j)
+            if (vols[j] == vols[i]) return PF_ERR_INVALID_ARG;  // a volume holds one sequence's state
+        pf_status st = pf::check_intrinsics(intrs + i);
+        if (st != PF_OK) return st;
+        st = check_params(params + i);
+        if (st != PF_OK) return st;
+        if (vols[i]->device != vols[0]->device) return PF_ERR_INVALID_ARG;
+        if (vols[i]->desc.tsdf_dtype != vols[0]->desc.tsdf_dtype) return PF_ERR_UNSUPPORTED;
+        const int layout = resolve_layout(vols[i]);
+        if (layout == 1 || layout != resolve_layout(vols[0])) return PF_ERR_UNSUPPORTED;
+    }
+    pf_batch* b = new pf_batch();
+    b->n = n;
+    b->vols.assign(vols, vols + n);
+    b->intrs.assign(intrs, intrs + n);
+    b->params.assign(params, params + n);
+    b->layout = resolve_layout(vols[0]);
+    b->dtype = vols[0]->desc.tsdf_dtype;
+    b->device = vols[0]->device;
+    b->use_graph = use_graph != 0;
+    size_t depth_total = 0;
+    for (int i = 0; i < n; ++i) {
+        b->max_iters = std::max(b->max_iters, params[i].n_iters);
+        b->depth_off.push_back(depth_total);
+        depth_total += ((size_t)intrs[i].width * intrs[i].height + 63) / 64 * 64;
+    }
+    auto fail = [&](pf_status st) {
+        pf_batch_destroy(b);
+        return st;
+    };
+    pf_status st = PF_OK;
+    for (int i = 0; i < n && st == PF_OK; ++i) {
+        pf_workspace& w = vols[i]->ws;
+        st = pf::workspace_reserve(vols[i], std::max(intrs[i].width * intrs[i].height, w.pix_cap),
+                                   std::max(params[i].k_max, w.k_cap));
+    }
+    if (st != PF_OK) return fail(st);
+    cudaError_t e = cudaMalloc(&b->depth, depth_total * sizeof(float));
+    if (e == cudaSuccess) e = cudaMemset(b->depth, 0, depth_total * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc(&b->poses, (size_t)n * 64 * sizeof(double));
+    if (e == cudaSuccess) e = cudaMemset(b->poses, 0, (size_t)n * 64 * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc(&b->stats, (size_t)n * sizeof(pf_track_stats));
+    if (e == cudaSuccess) e = cudaMemset(b->stats, 0, (size_t)n * sizeof(pf_track_stats));
+    if (e == cudaSuccess) e = cudaMalloc(&b->tune_state, (size_t)n * sizeof(SearchState));
+    if (e == cudaSuccess) e = cudaMalloc(&b->tune_stats, (size_t)n * sizeof(pf_track_stats));
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return fail(pf::cuda_status(e));
+    // identity poses
+    std::vector<double> I((size_t)n * 64, 0.0);
+    for (int i = 0; i < n; ++i)
+        for (int k = 0; k < 4; ++k)
+            for (int q = 0; q < 4; ++q) I[64 * (size_t)i + 16 * k + 5 * q] = 1.0;
+    e = cudaMemcpy(b->poses, I.data(), I.size() * sizeof(double), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return fail(pf::cuda_status(e));
+    st = batch_tables(b, false);
+    if (st != PF_OK) return fail(st);
+    *out = b;
+    return PF_OK;
+}
+
+pf_status pf_batch_destroy(pf_batch* b)
+{
+    if (!b) return PF_OK;
+    cudaDeviceSynchronize();
+    batch_drop_graph(b);
+    if (b->cap) cudaStreamDestroy(b->cap);
+    cudaFree(b->depth);
+    cudaFree(b->poses);
+    cudaFree(b->stats);
+    cudaFree(b->d_args);
+    cudaFree(b->d_first);
+    cudaFree(b->tune_state);
+    cudaFree(b->tune_stats);
+    delete b;
+    return PF_OK;
+}
+
+pf_status pf_batch_buffers(pf_batch* b, int i, float** depth_dev, double** rel_pose_dev, double** pose_dev,
+                           pf_track_stats** stats_dev)
+{
+    if (!b || i < 0 || i >= b->n) return PF_ERR_INVALID_ARG;
+    if (depth_dev) *depth_dev = b->depth + b->depth_off[i];
+    if (rel_pose_dev) *rel_pose_dev = b->rel(i);
+    if (pose_dev) *pose_dev = b->pose(i);
+    if (stats_dev) *stats_dev = b->stats + i;
+    return PF_OK;
+}
+
+pf_status pf_batch_fuse(pf_batch* b, void* stream)
+{
+    if (!b) return PF_ERR_INVALID_ARG;
+    for (int i = 0; i < b->n; ++i) {
+        pf_status st = pf_integrate_async(b->vols[i], b->depth + b->depth_off[i], &b->intrs[i], b->pose(i), stream);
+        if (st != PF_OK) return st;
+    }
+    return PF_OK;
+}
+
+pf_status pf_batch_step(pf_batch* b, void* stream)
+{
+    if (!b) return PF_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (!b->use_graph) return batch_enqueue(b, s);
+    if (!b->exec) {
+        const bool timing = pf::timing_swap(false);
+        const unsigned long long c0 = pf::g_launches.load();
+        cudaError_t e = cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal);
+        pf_status st = e == cudaSuccess ? batch_enqueue(b, b->cap) : pf::cuda_status(e);
+        cudaGraph_t g = nullptr;
+        const cudaError_t e2 = cudaStreamEndCapture(b->cap, &g);
+        const unsigned long long c1 = pf::g_launches.load();
+        pf::g_launches.fetch_sub(c1 - c0);
+        pf::timing_swap(timing);
+        if (st == PF_OK && e2 != cudaSuccess) st = pf::cuda_status(e2);
+        if (st != PF_OK) {
+            if (g) cudaGraphDestroy(g);
+            return st;
+        }
+        b->graph = g;
+        b->launches_per_step = c1 - c0;
+        PF_CUDA(cudaGraphInstantiate(&b->exec, b->graph, 0));
+    }
+    PF_CUDA(cudaGraphLaunch(b->exec, s));
+    pf::count_launch((unsigned)b->launches_per_step);
+    return PF_OK;
+}
+
+pf_status pf_batch_set_points_per_block(pf_batch* b, int points_per_block)
+{
+    if (!b || points_per_block < SUBTILE || points_per_block > (1 << 24)) return PF_ERR_INVALID_ARG;
+    PF_CUDA(cudaDeviceSynchronize());
+    b->points_per_block = points_per_block;
+    batch_drop_graph(b);
+    return batch_tables(b, false);
+}
+
+// Times the batched search launch of iteration 0 on copies of the search
+// state, once with the initial search size (lanes on points) and once with
+// it scaled by 1e-3 (lanes on particles, the contracted search), for each
+// candidate points-per-CTA, and keeps the fastest (weights 1 : 3, about the
+// share of the two regimes in a 20-iteration search).
+pf_status pf_batch_autotune(pf_batch* b, void* stream, int* chosen)
+{
+    if (!b) return PF_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    for (int i = 0; i < b->n; ++i) {
+        pf_volume* v = b->vols[i];
+        pf_status st = enqueue_backproject(b->depth + b->depth_off[i], &b->intrs[i], v->ws.points,
+                                           v->ws.block_counts, v->ws.n_points, s);
+        if (st != PF_OK) return st;
+    }
+    cudaEvent_t e0, e1;
+    PF_CUDA(cudaEventCreate(&e0));
+    PF_CUDA(cudaEventCreate(&e1));
+    const int candidates[] = {1024, 2048, 4096, 8192, 16384, 32768, 65536, 131072};
+    const int saved = b->points_per_block;
+    int best = saved;
+    float best_ms = INFINITY;
+    pf_status st = PF_OK;
+    for (int c : candidates) {
+        b->points_per_block = c;
+        st = batch_tables(b, true);
+        if (st != PF_OK) break;
+        float total = 0.0f;
+        for (int regime = 0; regime < 2 && st == PF_OK; ++regime) {
+            const double f = regime == 0 ? 1.0 : 1e-3;
+            for (int rep = 0; rep < 2; ++rep) {  // the first run warms up
+                for (int i = 0; i < b->n; ++i)
+                    track_begin_kernel<<<1, 32, 0, s>>>(b->tune_state + i, b->pose(i), b->params[i].init_rot_deg * f,
+                                                        b->params[i].init_trans_cm * f, b->tune_stats + i);
+                cudaEventRecord(e0, s);
+                launch_batch<SRC_SEARCH>(b, 0, 0, s);
+                cudaEventRecord(e1, s);
+                if (cudaEventSynchronize(e1) != cudaSuccess) {
+                    st = PF_ERR_CUDA;
+                    break;
+                }
+                float ms = 0.0f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                if (rep == 1) total += (regime == 0 ? 1.0f : 3.0f) * ms;
+            }
+        }
+        if (st != PF_OK) break;
+        if (total < best_ms) {
+            best_ms = total;
+            best = c;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    b->points_per_block = st == PF_OK ? best : saved;
+    batch_drop_graph(b);
+    pf_status st2 = batch_tables(b, false);
+    if (chosen) *chosen = b->points_per_block;
+    return st != PF_OK ? st : st2;
+}
+
+}  // extern "C"
+
 namespace {
 
 struct NoAllocScratch {

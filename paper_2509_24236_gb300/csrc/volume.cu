@@ -46,8 +46,8 @@ struct IntegArgs {
     float plane[4][3];                  // inward normals of the four side planes of the frustum
     float zfar;                         // nodes deeper than this are never updated
     float radius;                       // bounding radius of a tile (+ margin)
-    int* tile_stamp;                    // tiles not culled get `stamp` (null: no cell view)
-    int stamp;
+    int* tile_stamp;                    // tiles not culled get *stamp_dev (null: no cell view)
+    const int* stamp_dev;               // fusion counter on the device
 };
 
 template <typename TS, typename TW>
@@ -89,7 +89,7 @@ __global__ void __launch_bounds__(TX * TY, 4) integrate_kernel(IntegArgs a)
         }
         s_skip = skip;
         if (!skip && a.tile_stamp)
-            a.tile_stamp[blockIdx.x + gridDim.x * (blockIdx.y + (size_t)gridDim.y * blockIdx.z)] = a.stamp;
+            a.tile_stamp[blockIdx.x + gridDim.x * (blockIdx.y + (size_t)gridDim.y * blockIdx.z)] = *a.stamp_dev;
     }
     __syncthreads();
     if (s_skip) return;
@@ -160,7 +160,7 @@ struct RefreshArgs {
     void* cells;
     int nx, ny, nz;
     const int* tile_stamp;
-    int stamp;
+    const int* stamp_dev;
     int all;
 };
 
@@ -194,7 +194,7 @@ __global__ void __launch_bounds__(TX * TY, 4) cells_refresh_kernel(RefreshArgs a
         for (int q = 0; q < 8 && !need; ++q) {
             const unsigned bx = blockIdx.x + (q & 1), by = blockIdx.y + ((q >> 1) & 1), bz = blockIdx.z + (q >> 2);
             if (bx < gridDim.x && by < gridDim.y && bz < gridDim.z)
-                need = a.tile_stamp[bx + gridDim.x * (by + (size_t)gridDim.y * bz)] == a.stamp;
+                need = a.tile_stamp[bx + gridDim.x * (by + (size_t)gridDim.y * bz)] == *a.stamp_dev;
         }
         s_need = need;
     }
@@ -223,7 +223,7 @@ pf_status enqueue_refresh(pf_volume* v, cudaStream_t s, int all)
     r.ny = v->desc.ny;
     r.nz = v->desc.nz;
     r.tile_stamp = v->tile_stamp;
-    r.stamp = v->stamp;
+    r.stamp_dev = v->tile_stamp + (size_t)v->tiles[0] * v->tiles[1] * v->tiles[2];
     r.all = all;
     dim3 grid(v->tiles[0], v->tiles[1], v->tiles[2]);
     switch (v->desc.tsdf_dtype) {
@@ -327,9 +327,9 @@ pf_status pf_create_volume(const pf_volume_desc* desc, void* stream, pf_volume**
     if (e == cudaSuccess) e = cudaMalloc(&v->weight, v->n_nodes * ws);
     if (e == cudaSuccess && view) e = cudaMalloc(&v->cells, view_bytes);
     if (e == cudaSuccess && view)
-        e = cudaMalloc(&v->tile_stamp, sizeof(int) * (size_t)v->tiles[0] * v->tiles[1] * v->tiles[2]);
+        e = cudaMalloc(&v->tile_stamp, sizeof(int) * ((size_t)v->tiles[0] * v->tiles[1] * v->tiles[2] + 1));
     if (e == cudaSuccess && view)
-        e = cudaMemset(v->tile_stamp, 0, sizeof(int) * (size_t)v->tiles[0] * v->tiles[1] * v->tiles[2]);
+        e = cudaMemset(v->tile_stamp, 0, sizeof(int) * ((size_t)v->tiles[0] * v->tiles[1] * v->tiles[2] + 1));
     if (e != cudaSuccess) {
         cudaFree(v->tsdf);
         cudaFree(v->weight);
@@ -462,6 +462,11 @@ pf_status pf_volume_download(const pf_volume* v, float* tsdf_host, float* weight
 
 namespace {
 
+__global__ void stamp_bump_kernel(int* counter)
+{
+    if (threadIdx.x == 0) *counter += 1;
+}
+
 pf_status integrate_impl(pf_volume* v, const float* depth_dev, const pf_intrinsics* intr, const double* P_host,
                          const double* P_dev, cudaStream_t s)
 {
@@ -495,8 +500,17 @@ pf_status integrate_impl(pf_volume* v, const float* depth_dev, const pf_intrinsi
     const double vs = d.voxel_size;
     a.radius = (float)(0.5 * vs * sqrt((double)((TX - 1) * (TX - 1) + (TY - 1) * (TY - 1) + (TZ - 1) * (TZ - 1)))
                        + 0.01 * vs + 1e-3);
+    // the fusion counter lives on the device (after the per-tile stamps), so
+    // a captured and replayed launch sequence still marks each fusion apart
+    const size_t n_tiles = (size_t)v->tiles[0] * v->tiles[1] * v->tiles[2];
     a.tile_stamp = v->tile_stamp;
-    a.stamp = ++v->stamp;
+    a.stamp_dev = v->tile_stamp ? v->tile_stamp + n_tiles : nullptr;
+    ++v->stamp;
+    if (v->tile_stamp) {
+        stamp_bump_kernel<<<1, 1, 0, s>>>(v->tile_stamp + n_tiles);
+        pf::count_launch();
+        PF_LAUNCHED();
+    }
     dim3 grid(v->tiles[0], v->tiles[1], v->tiles[2]);
     pf::timing_begin(pf::KC_INTEGRATE, s);
     dispatch_storage<IntegrateLaunch>(v, grid, a, s);

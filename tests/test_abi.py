@@ -83,6 +83,12 @@ def test_host_side_validation_without_a_gpu(lib):
     assert lib.pf_align_loss(None, None, None, 0, 1, None, None, None, None, None, None, None,
                              None) == pf.PF_ERR_INVALID_ARG
     assert lib.pf_polish(None, None, None, 0, None, 10, None, None, None) == pf.PF_ERR_INVALID_ARG
+    bout = C.c_void_p()
+    assert lib.pf_batch_create(0, None, None, None, 1, C.byref(bout)) == pf.PF_ERR_INVALID_ARG
+    assert lib.pf_batch_create(1, (C.c_void_p * 1)(None), C.byref(intr), None, 1,
+                               C.byref(bout)) == pf.PF_ERR_INVALID_ARG
+    assert lib.pf_batch_step(None, None) == pf.PF_ERR_INVALID_ARG
+    assert lib.pf_batch_buffers(None, 0, None, None, None, None) == pf.PF_ERR_INVALID_ARG
     bad_intr = pf.pf_intrinsics(0, 3, 2.0, 2.0, 1.5, 1.0, 0.1, 8.0)
     assert lib.pf_backproject(C.c_void_p(1), C.byref(bad_intr), C.c_void_p(1), 100, C.c_void_p(1),
                               None) == pf.PF_ERR_INVALID_ARG

@@ -1,0 +1,143 @@
+"""Batches of sequences (pf_batch_*): several volumes of different sizes and
+cameras stepped together, the search iterations of all sequences sharing
+launches, the step captured in a CUDA graph.
+
+Each sequence's search is checked against the FP64 oracle exactly as a
+single-sequence search is (same best particle and advantage-set size while
+the oracle's margins are clear, final pose within 1e-4 m / 1e-4 rad);
+graph replay must be bit-identical to direct launches; the autotuner must
+pick one of its candidates and leave the batch usable.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from synth import Grid, Intrinsics
+
+from gpu_helpers import abi, load_pf, pose_rot_err, pose_trans_err, to_dev, torch_cuda
+
+pytestmark = pytest.mark.gpu
+
+# (grid, camera, view): three sequences of unequal size over the room scene
+SEQS = [
+    (synth.ROOM64_GRID, synth.ROOM64_INTR, 0),
+    (Grid(48, 40, 44, 0.07, 0.21, (0.0, 0.0, 0.0)), Intrinsics(200, 150, 175.0, 176.0, 99.3, 74.8, 0.1, 8.0), 1),
+    (Grid(80, 80, 80, 0.04, 0.12, (0.0, 0.0, 0.0)), Intrinsics(320, 240, 280.0, 280.0, 159.5, 119.5, 0.1, 8.0), 2),
+]
+K, ITERS = 1024, 10
+
+
+@pytest.fixture(scope="module")
+def pf():
+    torch_cuda()
+    return load_pf()
+
+
+def _setup(pf, seed=0):
+    """Volumes fused from three noise-free views each, the frame to track
+    (noisy) and its initial pose per sequence."""
+    torch = torch_cuda()
+    scene = synth.room_scene(seed)
+    vols, frames = [], []
+    for g, intr, view in SEQS:
+        v = pf.Volume.from_grid(g)
+        for j in range(3):
+            P = synth.room_view(scene, (view + 1 + j) % 8)
+            v.integrate(to_dev(synth.render_depth(scene, intr, P)), intr, P)
+        gt = synth.room_view(scene, view)
+        depth = synth.add_depth_noise(synth.render_depth(scene, intr, gt), 60 + view, 0.001)
+        init = gt @ synth.perturbation(70 + view, 0, 3.0, 3.0)
+        vols.append(v)
+        frames.append((depth, gt, init))
+    torch.cuda.synchronize()
+    templ = torch.from_numpy(synth.templates(K, seed)).cuda()
+    params = [pf.track_params(templ, n_iters=ITERS, k_sched=(K, K, K), decim_sched=(1, 1, 1), update_mode=0,
+                              compose_mode=1) for _ in SEQS]
+    return vols, frames, templ, params
+
+
+def _load_inputs(batch, frames):
+    for i, (depth, gt, init) in enumerate(frames):
+        batch.depth[i].copy_(to_dev(depth))
+        batch.pose[i].copy_(to_dev(init))
+        batch.rel[i].copy_(to_dev(np.eye(4)))
+
+
+def test_batch_step_matches_the_oracle_per_sequence(pf):
+    torch = torch_cuda()
+    vols, frames, templ, params = _setup(pf)
+    grids = [v.download() for v in vols]  # the state each search runs against
+    batch = pf.Batch(vols, [s[1] for s in SEQS], params, use_graph=True)
+    _load_inputs(batch, frames)
+    batch.step()
+    torch.cuda.synchronize()
+    oparams = oracle.TrackParams(n_iters=ITERS, k_sched=(K, K, K), decim_sched=(1, 1, 1), update_mode=0,
+                                 compose_mode=1)
+    for i, ((g, intr, view), (depth, gt, init)) in enumerate(zip(SEQS, frames)):
+        st = batch.stats_dict(i)
+        pose = batch.pose[i].cpu().numpy()
+        ovol = oracle.Volume(abi(g), *grids[i])
+        ores = oracle.track(ovol, depth, abi(intr), templ.cpu().numpy(), init, oparams)
+        assert st["status"] == pf.PF_OK and not ores.lost
+        os_ = ores.stats
+        assert st["n_points"] == os_["n_points"]
+        strict = 0
+        for it in range(ITERS):
+            if not (os_["best_gap"][it] > 3e-5 and os_["adv_margin"][it] > 3e-5):
+                break
+            strict += 1
+            assert st["best"][it] == os_["best"][it] and st["n_adv"][it] == os_["n_adv"][it], (i, it)
+        assert strict >= 2, i
+        assert pose_trans_err(pose, ores.pose) <= 1e-4 and pose_rot_err(pose, ores.pose) <= 1e-4, i
+    batch.close()
+
+
+def test_graph_replay_equals_direct_launches(pf):
+    torch = torch_cuda()
+    results = []
+    for use_graph in (False, True):
+        vols, frames, templ, params = _setup(pf)
+        batch = pf.Batch(vols, [s[1] for s in SEQS], params, use_graph=use_graph)
+        _load_inputs(batch, frames)
+        out = []
+        for step in range(3):
+            # the same frame again, from a pose nudged away from the last result
+            for i in range(batch.n):
+                batch.rel[i].copy_(to_dev(synth.perturbation(80 + step, i, 1.0, 1.0)))
+            batch.step()
+            torch.cuda.synchronize()
+            out.append([(batch.pose[i].cpu().numpy().copy(), batch.stats[i].cpu().numpy().copy())
+                        for i in range(batch.n)])
+        tsdf = [v.download()[0] for v in vols]
+        results.append((out, tsdf))
+        batch.close()
+    (o1, t1), (o2, t2) = results
+    for s1, s2 in zip(o1, o2):
+        for (p1, st1), (p2, st2) in zip(s1, s2):
+            assert np.array_equal(p1, p2) and np.array_equal(st1, st2)
+    for a, b in zip(t1, t2):
+        assert np.array_equal(a, b, equal_nan=True)
+
+
+def test_autotune_and_validation(pf):
+    torch = torch_cuda()
+    vols, frames, templ, params = _setup(pf)
+    batch = pf.Batch(vols, [s[1] for s in SEQS], params, use_graph=True)
+    _load_inputs(batch, frames)
+    batch.step()  # captures
+    p = batch.autotune()
+    assert p in (1024, 2048, 4096, 8192, 16384, 32768, 65536, 131072)
+    batch.step()  # recaptures with the chosen tiling
+    torch.cuda.synchronize()
+    for i in range(batch.n):
+        assert batch.stats_dict(i)["status"] == pf.PF_OK
+    with pytest.raises(pf.ProfusionError):
+        batch.set_points_per_block(100)
+    batch.close()
+    # a volume may appear once; storage types may not mix
+    with pytest.raises(pf.ProfusionError):
+        pf.Batch([vols[0], vols[0]], [SEQS[0][1]] * 2, params[:2])
+    v16 = pf.Volume.from_grid(SEQS[0][0], tsdf_dtype=pf.PF_F16)
+    with pytest.raises(pf.ProfusionError):
+        pf.Batch([vols[0], v16], [SEQS[0][1]] * 2, params[:2])
