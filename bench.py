@@ -56,15 +56,22 @@ def parse():
     ap.add_argument("--tsdf-dtype", default="f32", choices=["f32", "f16", "bf16"],
                     help="storage type of the TSDF and its cell view (arithmetic stays f32)")
     ap.add_argument("--weight-u8", action="store_true", help="store fusion weights as uint8")
+    ap.add_argument("--schedule", default="fixed", choices=["fixed", "paper"],
+                    help="fixed: 3072 particles x 20 iterations over all points (the benchmark configuration); "
+                         "paper: particles alternating 1024/3072/10240 with points decimated 1/8, 1/16, 1/32")
+    ap.add_argument("--frame-step", type=int, default=1,
+                    help="process every n-th frame of the trajectory (frames in between dropped)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ref-particles", type=int, default=192,
                     help="particles per reference-arm step (a bounded slice of one iteration)")
-    ap.add_argument("--kernel", default=None, choices=["fitness", "integrate", "align", "batch"],
+    ap.add_argument("--kernel", default=None, choices=["fitness", "integrate", "align", "batch", "room64"],
                     help="time one kernel on the multiroom volume instead of the frame loop (profiling); "
                          "align: loss + pose and node gradients of 64 320x240 frames against a 256^3 volume, "
                          "and the 10-step polish; batch: 32 sequences of mixed camera and volume size stepped "
-                         "together (pf_batch, CUDA graph) against the same sequences one after another")
+                         "together (pf_batch, CUDA graph) against the same sequences one after another; room64: "
+                         "the single-frame room workload (160x120, 64^3 at 5 cm, 1024 particles x 10 iterations, "
+                         "seeds 0-9) with each layout, and the oracle on the host")
     ap.add_argument("--spread", type=float, default=3.0,
                     help="--kernel fitness: poses perturbed up to this many degrees and centimetres")
     ap.add_argument("--reps", type=int, default=3, help="--kernel: timed launches after one warm-up launch")
@@ -77,19 +84,20 @@ def parse():
 
 def _render(args):
     import synth
-    n_frames, seed, f = args
+    n_frames, seed, f, step = args
     seq = synth.multiroom_sequence(n_frames, seed)
-    return seq.depth(f), seq.relative_init(f) if f > 0 else np.eye(4)
+    return seq.depth(f * step), seq.relative_init(f * step, step) if f > 0 else np.eye(4)
 
 
-def render_frames(n_needed: int, seed: int):
-    """Depth frames 0..n_needed-1 and perturbed relative poses, rendered in a
-    spawn pool (started before any CUDA call)."""
+def render_frames(n_needed: int, seed: int, step: int = 1):
+    """Depth frames 0, step, ..., (n_needed-1) step and the perturbed relative
+    poses between consecutive ones, rendered in a spawn pool (started before
+    any CUDA call)."""
     import multiprocessing as mp
 
     import synth
     seq = synth.multiroom_sequence(300, seed)
-    jobs = [(300, seed, f) for f in range(n_needed)]
+    jobs = [(300, seed, f, step) for f in range(n_needed)]
     workers = max(1, min(len(jobs), (os.cpu_count() or 2) - 1, 16))
     if workers > 1:
         with mp.get_context("spawn").Pool(workers) as pool:
@@ -257,7 +265,7 @@ def run_reference(args):
 
 
 def storage_desc(args) -> str:
-    return f"{args.tsdf_dtype} tsdf + {'u8' if args.weight_u8 else 'f32'} weight"
+    return f"{getattr(args, 'tsdf_dtype', 'f32')} tsdf + {'u8' if getattr(args, 'weight_u8', False) else 'f32'} weight"
 
 
 def new_volume(pf, grid, args):
@@ -265,12 +273,26 @@ def new_volume(pf, grid, args):
     return pf.Volume.from_grid(grid, tsdf_dtype=dt, weight_u8=int(args.weight_u8))
 
 
+def schedule(args):
+    """(k_sched, decim_sched, k_max) of the search."""
+    if getattr(args, "schedule", "fixed") == "paper":
+        return (1024, 3072, 10240), (8, 16, 32), 10240
+    return (K_PARTICLES,) * 3, (1, 1, 1), K_PARTICLES
+
+
 def workload_config(args) -> dict:
+    paper = getattr(args, "schedule", "fixed") == "paper"
+    step = getattr(args, "frame_step", 1)
+    search = ("3072 particles x 20 iterations over all points" if not paper else
+              "20 iterations, particles 1024/3072/10240 with points decimated 1/8, 1/16, 1/32 (paper schedule)")
+    drop = "" if step == 1 else f", every {step}th frame (the others dropped)"
+    k_sched, d_sched, _ = schedule(args)
     return {
         "workload": f"multiroom: 640x480 depth, 512^3 TSDF @ 1 cm (tau 3 cm, {storage_desc(args)}), "
-                    "3072 particles x 20 iterations over all points, then fusion",
+                    f"{search}, then fusion{drop}",
         "resolution": "640x480", "volume": "512^3", "voxel_m": 0.01, "trunc_m": 0.03,
-        "particles": K_PARTICLES, "iterations": N_ITERS, "decimation": 1,
+        "particles": list(k_sched) if paper else K_PARTICLES, "iterations": N_ITERS,
+        "decimation": list(d_sched) if paper else 1, "frame_step": step,
         "update": "advantage-set mean" if args.update_mode == 0 else "best particle",
         "compose": "about the world origin" if args.compose_mode == 0 else "about the camera centre",
         "init_perturbation": "3 deg / 3 cm", "seed": args.seed,
@@ -288,9 +310,11 @@ def run_ours(args):
     world, rank, local = world_info()
     W, K = max(3, args.warmup), max(1, args.steps)
     n_frames = 1 + W + K
-    if n_frames > 300:
-        raise SystemExit("--warmup + --steps must be <= 299 (300-frame trajectory)")
-    seq, depths, rels = render_frames(n_frames, replica_seed(args.seed, rank))
+    step = max(1, args.frame_step)
+    if (n_frames - 1) * step > 299:
+        raise SystemExit("(--warmup + --steps) x --frame-step must be <= 299 (300-frame trajectory)")
+    seq, depths, rels = render_frames(n_frames, replica_seed(args.seed, rank), step)
+    gt = [seq.gt[f * step] for f in range(n_frames)]  # the processed frames
 
     import torch
     import paper_2509_24236_gb300 as pf
@@ -312,10 +336,11 @@ def run_ours(args):
     stream = torch.cuda.current_stream()
     vol = new_volume(pf, grid, args)
     vol.set_fitness_variant(args.variant)
-    vol.reserve(intr.width * intr.height, K_PARTICLES)
+    k_sched, d_sched, k_max = schedule(args)
+    vol.reserve(intr.width * intr.height, k_max)
     import synth
-    templ = torch.from_numpy(synth.templates(K_PARTICLES, args.seed)).to(dev)
-    params = pf.track_params(templ, n_iters=N_ITERS, k_sched=(K_PARTICLES,) * 3, decim_sched=(1, 1, 1),
+    templ = torch.from_numpy(synth.templates(k_max, args.seed)).to(dev)
+    params = pf.track_params(templ, n_iters=N_ITERS, k_sched=k_sched, decim_sched=d_sched,
                              update_mode=args.update_mode, compose_mode=args.compose_mode, min_valid_frac=0.05)
     depth_dev = [torch.from_numpy(d).to(dev) for d in depths]
     rel_dev = torch.from_numpy(np.stack([r.reshape(16) for r in rels])).to(dev)
@@ -323,7 +348,7 @@ def run_ours(args):
     pose_dev = torch.zeros((n_frames, 16), dtype=torch.float64, device=dev)
     stats_sz = __import__("ctypes").sizeof(pf.pf_track_stats)
     stats_dev = torch.zeros((n_frames, stats_sz), dtype=torch.uint8, device=dev)
-    pose_dev[0] = torch.from_numpy(seq.gt[0].reshape(16)).to(dev)
+    pose_dev[0] = torch.from_numpy(gt[0].reshape(16)).to(dev)
 
     def device_frame(f):
         pf.pf_pose_compose(pose_dev[f - 1], rel_dev[f], init_dev[f])
@@ -368,7 +393,7 @@ def run_ours(args):
         samples += int(np.sum(st["k_used"].astype(np.int64) * st["n_eval"]))
         n_lost += int(st["status"] == pf.PF_ERR_TRACK_LOST)
     poses = pose_dev.cpu().numpy().reshape(-1, 4, 4)
-    err = [np.linalg.norm(poses[f][:3, 3] - seq.gt[f][:3, 3]) for f in range(1, W + K + 1)]
+    err = [np.linalg.norm(poses[f][:3, 3] - gt[f][:3, 3]) for f in range(1, W + K + 1)]
     ate_cm = 100.0 * float(np.sqrt(np.mean(np.square(err))))
 
     # ---- fitness kernel throughput, encoded vs plain layout --------------
@@ -379,7 +404,7 @@ def run_ours(args):
     # ---- end-to-end pass through the host API ----------------------------
     e2e = None
     if not args.no_e2e:
-        e2e = run_e2e(pf, vol, seq, depths, rels, intr, params, W, K, dev)
+        e2e = run_e2e(pf, vol, gt, depths, rels, intr, params, W, K, dev)
 
     value = job_rate(K, world, ms_max)
     fit_ms, fit_n = kt["fitness"]
@@ -405,7 +430,7 @@ def run_ours(args):
         "ate_cm": ate_cm, "frames_lost": n_lost,
         "e2e": e2e,
     }
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and args.schedule == "fixed":
         fps, desc, cores, times, t_int, npts = oracle_sample(seq, depths, rels, args.compose_mode, 1024, repeats=1)
         line["cpu_baseline"] = {"value": fps, "unit": "frames/s", "cores": cores, "kind": "oracle", "sample": desc}
     if rank == 0:
@@ -480,12 +505,12 @@ def fitness_vs_plain(pf, vol, depth, intr, pose, dev, reps=5):
     return out
 
 
-def run_e2e(pf, vol, seq, depths, rels, intr, params, W, K, dev):
+def run_e2e(pf, vol, gt, depths, rels, intr, params, W, K, dev):
     import torch
     vol.reset()
     pinned = [torch.from_numpy(d).pin_memory() for d in depths]
     buf = torch.empty_like(pinned[0], device=dev)
-    P = seq.gt[0].copy()
+    P = gt[0].copy()
     buf.copy_(pinned[0], non_blocking=True)
     vol.integrate(buf, intr, P)
 
@@ -788,8 +813,84 @@ def run_batch(args):
     return 0
 
 
+def run_room64(args):
+    """The single-frame room workload: 160x120 depth (1 mm noise) of the
+    3.2 m room with three spheres, a 64^3 TSDF at 5 cm (tau 15 cm) of the
+    analytic scene, initial pose 5 deg / 5 cm off, 1024 particles x 10
+    iterations over all points, mean update; seeds 0-9.  Device ms per frame
+    (pf_track_frame_async, CUDA events over --reps repeats) for the default
+    kernel and the plain float layout, pose error, and the oracle's time for
+    the same frames on the host cores."""
+    import time
+
+    import synth
+    seeds = list(range(10))
+    frames = [synth.room64_frame(sd) for sd in seeds]
+    vols_np = [synth.analytic_tsdf(sc, synth.ROOM64_GRID, hole_bricks=0.0, seed=sd) for (sc, fr), sd in
+               zip(frames, seeds)]
+    K, I = 1024, 10
+    templ_np = synth.templates(K, 0)
+    # oracle on the host (before any CUDA call)
+    import oracle
+    oracle.build()
+    t0 = time.perf_counter()
+    for (sc, fr), (t, w) in zip(frames, vols_np):
+        ov = oracle.Volume(synth.ROOM64_GRID, t, w)
+        oracle.track(ov, fr.depth, synth.ROOM64_INTR, templ_np, fr.init_pose,
+                     oracle.TrackParams(n_iters=I, k_sched=(K, K, K), decim_sched=(1, 1, 1), update_mode=0,
+                                        compose_mode=args.compose_mode))
+    oracle_ms = (time.perf_counter() - t0) / len(seeds) * 1e3
+    import torch
+
+    import paper_2509_24236_gb300 as pf
+    from paper_2509_24236_gb300 import build as pfbuild
+    pfbuild.build()
+    pf.load()
+    dev = torch.device("cuda", 0)
+    templ = torch.from_numpy(templ_np).to(dev)
+    params = pf.track_params(templ, n_iters=I, k_sched=(K, K, K), decim_sched=(1, 1, 1), update_mode=0,
+                             compose_mode=args.compose_mode)
+    out = {}
+    for name, variant in (("default", 0), ("plain_f32", 1)):
+        ms, errs = [], []
+        for (sc, fr), (t, w) in zip(frames, vols_np):
+            vol = pf.Volume.from_grid(synth.ROOM64_GRID)
+            vol.upload(t, w)
+            vol.set_fitness_variant(variant)
+            vol.reserve(synth.ROOM64_INTR.width * synth.ROOM64_INTR.height, K)
+            d = torch.from_numpy(fr.depth).to(dev)
+            init = torch.from_numpy(fr.init_pose.reshape(16)).to(dev)
+            outp = torch.zeros(16, dtype=torch.float64, device=dev)
+            vol.track_frame_async(d, synth.ROOM64_INTR, params, init, outp)
+            torch.cuda.synchronize()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record()
+            for _ in range(args.reps):
+                vol.track_frame_async(d, synth.ROOM64_INTR, params, init, outp)
+            b.record()
+            torch.cuda.synchronize()
+            ms.append(a.elapsed_time(b) / args.reps)
+            P = outp.cpu().numpy().reshape(4, 4)
+            errs.append(float(np.linalg.norm(P[:3, 3] - fr.gt_pose[:3, 3])))
+            vol.close()
+        out[name] = {"ms_per_frame": float(np.mean(ms)), "frames_per_s": 1e3 / float(np.mean(ms)),
+                     "samples_per_s": K * I * 19200 / (float(np.mean(ms)) / 1e3),
+                     "pose_error_cm_mean": 100 * float(np.mean(errs)), "pose_error_cm_max": 100 * float(np.max(errs))}
+    print(json.dumps({
+        "kernel": "room64", "workload": "160x120, 64^3 TSDF @ 5 cm (tau 15 cm), 1024 particles x 10 iterations, "
+                                        "all points, mean update, init 5 deg / 5 cm, seeds 0-9",
+        "reps": args.reps, "gpu": out,
+        "cpu_baseline": {"ms_per_frame": oracle_ms, "cores": oracle.num_threads(), "kind": "oracle",
+                         "sample": "the same 10 frames, full search"},
+    }))
+    return 0
+
+
 def main():
     args = parse()
+    if args.kernel == "room64":
+        return run_room64(args)
     if args.kernel == "batch":
         return run_batch(args)
     if args.kernel == "align":

@@ -356,17 +356,22 @@ PF_API pf_status pf_polish(const pf_volume* vol, const float* points_dev, const 
 /* Fitness kernel variant used by pf_fitness and the search of this volume,
  * variant = layout + 4 * mapping (0 is the default everywhere).
  *   layout  0: the cell view when the volume has one, else 2;
- *           1: the plain form: tsdf and weight arrays, all eight nodes
- *              tested explicitly (the performance baseline);
+ *           1: the plain float form, the performance baseline: every
+ *              sample's grid coordinate A x + c in float from the particle's
+ *              absolute transform, floor, an explicit range test, eight tsdf
+ *              and eight weight loads with all eight nodes tested; lanes on
+ *              points only (the mapping is ignored); float storage only;
  *           2: the tsdf array alone, whose encoding makes a cell's validity
  *              a property of its interpolated value;
  *           3: the cell view (PF_ERR_INVALID_ARG if the volume has none).
  *   mapping 0: chosen per block of points from the spread of the particles;
  *           1: neighbouring points on the lanes of a warp;
  *           2: particles on the lanes of a warp.
- * All variants evaluate the same samples: counts are identical and fitness
- * values differ only by the float summation order (layouts are bit-identical
- * for a given mapping). */
+ * Layouts 2 and 3 evaluate the same samples (bit-identical for a given
+ * mapping; mappings differ only by the float summation order).  Layout 1
+ * rounds each sample position once at the scale of the grid coordinate
+ * (instead of forming it from exact reference products), so its values
+ * differ from the others by that rounding. */
 PF_API pf_status pf_set_fitness_variant(pf_volume* vol, int variant);
 
 PF_API const char* pf_status_string(pf_status status);

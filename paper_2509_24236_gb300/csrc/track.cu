@@ -342,10 +342,18 @@ __device__ inline void particle_pose(const FitArgs& a, int k, double R[9], doubl
     }
 }
 
+// A particle as the plain float form uses it: grid coordinate = A x + c,
+// A = R / vs, c = (t - origin) / vs, both rounded to float.
+struct PlainXf {
+    float A[9];
+    float c[3];
+};
+
 // Particles k_begin .. k_begin+kc-1 into shared memory, and the chunk's
-// reference matrix A_ref (its first particle) as hi and lo floats.
+// reference matrix A_ref (its first particle) as hi and lo floats; with
+// sAbs, also each particle's plain float transform.
 template <int SRC>
-__device__ void build_particles(const FitArgs& a, int k_begin, int kc, Particle* sP, float* sRef)
+__device__ void build_particles(const FitArgs& a, int k_begin, int kc, Particle* sP, float* sRef, PlainXf* sAbs)
 {
     const int t = threadIdx.x;
     if (t >= kc) return;
@@ -365,6 +373,10 @@ __device__ void build_particles(const FitArgs& a, int k_begin, int kc, Particle*
         magic[r] = kMagicBits - (int)o;
     }
     if (!ok) magic[0] = kNeverValid;
+    if (sAbs) {
+        for (int q = 0; q < 9; ++q) sAbs[t].A[q] = (float)(R[q] * iv);
+        for (int r = 0; r < 3; ++r) sAbs[t].c[r] = (float)((tw[r] - a.org[r]) * iv);
+    }
     sP[t].d0 = make_float4(d[0], d[1], d[2], b[0]);
     sP[t].d1 = make_float4(d[3], d[4], d[5], b[1]);
     sP[t].d2 = make_float4(d[6], d[7], d[8], b[2]);
@@ -701,6 +713,7 @@ __device__ __forceinline__ void fitness_body(const FitArgs& a, int bx, int by, u
 {
     __shared__ Particle sP[KC];
     __shared__ ParticleD sPD[KC];
+    __shared__ PlainXf sAbs[VARIANT == 1 ? KC : 1];
     __shared__ float sRef[18];
     // particles on lanes: each warp's points as pairs (point q, point q + 64
     // of the warp): (x, y), (z, yf0), (yf1, yf2), and their reference cells
@@ -739,7 +752,7 @@ __device__ __forceinline__ void fitness_body(const FitArgs& a, int bx, int by, u
     __syncthreads();
     const bool skip = s_skip != 0;
     if (!skip) {
-        build_particles<SRC>(a, k_begin, kc, sP, sRef);
+        build_particles<SRC>(a, k_begin, kc, sP, sRef, VARIANT == 1 ? sAbs : nullptr);
         if (tid < kc) make_particle_d(sP[tid], nx, nxy, sPD[tid]);
     }
     __syncthreads();
@@ -806,6 +819,42 @@ __device__ __forceinline__ void fitness_body(const FitArgs& a, int bx, int by, u
                     py[p] = NAN;
                     pz[p] = NAN;
                 }
+            }
+            if (VARIANT == 1) {
+                // The plain float form (the performance baseline): for each
+                // particle, every point's grid coordinate A x + c in float,
+                // floor, an explicit range test, eight tsdf and eight weight
+                // loads; lanes on neighbouring points, warp-shuffle sums.
+                for (int kk = 0; kk < kc; ++kk) {
+                    const PlainXf& X = sAbs[kk];
+                    float s = 0.0f;
+                    int c = 0;
+#pragma unroll
+                    for (int p = 0; p < PPT; ++p) {
+                        const float gx = fmaf(X.A[0], px[p], fmaf(X.A[1], py[p], fmaf(X.A[2], pz[p], X.c[0])));
+                        const float gy = fmaf(X.A[3], px[p], fmaf(X.A[4], py[p], fmaf(X.A[5], pz[p], X.c[1])));
+                        const float gz = fmaf(X.A[6], px[p], fmaf(X.A[7], py[p], fmaf(X.A[8], pz[p], X.c[2])));
+                        if (!(gx >= 0.0f && gx < (float)(a.nx - 1) && gy >= 0.0f && gy < (float)(a.ny - 1) &&
+                              gz >= 0.0f && gz < (float)(a.nz - 1)))
+                            continue;
+                        const float fx0 = floorf(gx), fy0 = floorf(gy), fz0 = floorf(gz);
+                        Cell q;
+                        q.idx = (int)fx0 + nx * (int)fy0 + nxy * (int)fz0;
+                        q.fx = gx - fx0;
+                        q.fy = gy - fy0;
+                        q.fz = gz - fz0;
+                        q.ok = true;
+                        gather<1, float>(a, nx, nxy, q, s, c);
+                    }
+                    c = __reduce_add_sync(0xffffffffu, c);
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+                    if (lane == 0) {
+                        accS[warp][kk] += s;
+                        accC[warp][kk] += c;
+                    }
+                }
+                continue;
             }
             // mapping of this sub-tile: when every particle puts a point in
             // (nearly) the same cell, lanes take particles and share a point,

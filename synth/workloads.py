@@ -72,9 +72,10 @@ class Sequence:
             self._cache[f] = d
         return self._cache[f]
 
-    def relative_init(self, f: int) -> np.ndarray:
-        """Perturbed relative pose P_(f, f-1): P0_f = P_{f-1} @ relative_init(f)."""
-        return relative(self.gt[f - 1], self.gt[f]) @ perturbation(300 + self.seed, f, self.deg, self.cm)
+    def relative_init(self, f: int, step: int = 1) -> np.ndarray:
+        """Perturbed relative pose from frame f - step to frame f (the frames
+        in between dropped): P0_f = P_{f-step} @ relative_init(f, step)."""
+        return relative(self.gt[f - step], self.gt[f]) @ perturbation(300 + self.seed, f, self.deg, self.cm)
 
 
 @lru_cache(maxsize=4)
