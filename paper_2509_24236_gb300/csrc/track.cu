@@ -1268,14 +1268,30 @@ int device_sms(int dev)
 }
 
 // Point tiles for a launch with `chunks` particle chunks over at most
-// `ne_max` evaluated points: enough CTAs for about two full waves.
+// `ne_max` evaluated points.  The CTA count is chosen to fill whole waves of
+// resident CTAs (PF_FIT_MIN_BLOCKS per SM): among 3.5 to 8.5 waves, the
+// count whose last wave is fullest (the fewest waves on a tie) -- on the
+// 640x480 / 512^3 search, 4 exact waves run 9% faster than 2.7 waves.  Tiles
+// never go below one sub-tile of points; a launch too small for 3.5 waves
+// takes as many tiles as it has sub-tiles.
 int choose_ptiles(int dev, int chunks, long long ne_max)
 {
-    const long long target = (long long)device_sms(dev) * 4 * 2;
-    long long tiles = (target + chunks - 1) / chunks;
+    const long long cap = (long long)device_sms(dev) * PF_FIT_MIN_BLOCKS;
     const long long max_tiles = std::max(1LL, (ne_max + SUBTILE - 1) / SUBTILE);
-    tiles = std::min(tiles, max_tiles);
-    return (int)std::max(1LL, tiles);
+    long long best = 0;
+    double best_eff = 0.0;
+    for (long long t = 1; t <= max_tiles; ++t) {
+        const double waves = (double)(chunks * t) / (double)cap;
+        if (waves > 8.5) break;
+        if (waves < 3.5) continue;
+        const double eff = waves / std::ceil(waves);
+        if (eff > best_eff + 1e-9) {
+            best_eff = eff;
+            best = t;
+        }
+    }
+    if (best == 0) best = std::min(max_tiles, std::max(1LL, (long long)std::ceil(3.5 * cap / chunks)));
+    return (int)best;
 }
 
 // variant = layout + 4 * mapping (see pf_set_fitness_variant).  Measured on
