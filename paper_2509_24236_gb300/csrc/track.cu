@@ -444,6 +444,8 @@ __device__ __forceinline__ void accumulate(float t, float& s, int& c)
 
 // Trilinear interpolation from a cell-view record: corners with their
 // x-differences already formed (v000, v100 - v000, v010, v110 - v010, ...).
+// (A packed f32x2 form of these steps was measured slower: it needs the
+// fractions duplicated into register pairs.)
 __device__ __forceinline__ float trilerp_cell(float fx, float fy, float fz, float4 lo, float4 hi)
 {
     const float x00 = fmaf(fx, lo.y, lo.x);
@@ -974,29 +976,51 @@ __device__ __forceinline__ void fitness_body(const FitArgs& a, int bx, int by, u
                 load_xformd(sPD[kl], X);
                 float s = 0.0f;
                 int c = 0;
+                if (__all_sync(0xffffffffu, in_all)) {
+                    // every pair of the warp is interior: no range tests
 #pragma unroll 4
-                for (int j = 0; j < PPT * 16; ++j) {
-                    const float4 q0 = sPair[warp][j][0], q1 = sPair[warp][j][1], q2 = sPair[warp][j][2];
-                    const int2 yl = sPyl[warp][j];
-                    PointPair pp;
-                    pp.x = make_float2(q0.x, q0.y);
-                    pp.y = make_float2(q0.z, q0.w);
-                    pp.z = make_float2(q1.x, q1.y);
-                    pp.yf0 = make_float2(q1.z, q1.w);
-                    pp.yf1 = make_float2(q2.x, q2.y);
-                    pp.yf2 = make_float2(q2.z, q2.w);
-                    pp.yla = yl.x;
-                    pp.ylb = yl.y;
-                    Cell ca, cb;
-                    if (yl.x != INT_MIN) {  // the same for every lane
+                    for (int j = 0; j < PPT * 16; ++j) {
+                        const float4 q0 = sPair[warp][j][0], q1 = sPair[warp][j][1], q2 = sPair[warp][j][2];
+                        const int2 yl = sPyl[warp][j];
+                        PointPair pp;
+                        pp.x = make_float2(q0.x, q0.y);
+                        pp.y = make_float2(q0.z, q0.w);
+                        pp.z = make_float2(q1.x, q1.y);
+                        pp.yf0 = make_float2(q1.z, q1.w);
+                        pp.yf1 = make_float2(q2.x, q2.y);
+                        pp.yf2 = make_float2(q2.z, q2.w);
+                        pp.yla = yl.x;
+                        pp.ylb = yl.y;
+                        Cell ca, cb;
                         locate2<false>(X, nx, nxy, mx, my, mz, pp, nullptr, nullptr, ca, cb);
-                    } else {
-                        const int4 ya = sPyi[warp][j][0], yb = sPyi[warp][j][1];
-                        const int Ya[3] = {ya.x, ya.y, ya.z}, Yb[3] = {yb.x, yb.y, yb.z};
-                        locate2<true>(X, nx, nxy, mx, my, mz, pp, Ya, Yb, ca, cb);
+                        gather<VARIANT, TS, true>(a, nx, nxy, ca, s, c);
+                        gather<VARIANT, TS, true>(a, nx, nxy, cb, s, c);
                     }
-                    gather<VARIANT, TS, true>(a, nx, nxy, ca, s, c);
-                    gather<VARIANT, TS, true>(a, nx, nxy, cb, s, c);
+                } else {
+#pragma unroll 2
+                    for (int j = 0; j < PPT * 16; ++j) {
+                        const float4 q0 = sPair[warp][j][0], q1 = sPair[warp][j][1], q2 = sPair[warp][j][2];
+                        const int2 yl = sPyl[warp][j];
+                        PointPair pp;
+                        pp.x = make_float2(q0.x, q0.y);
+                        pp.y = make_float2(q0.z, q0.w);
+                        pp.z = make_float2(q1.x, q1.y);
+                        pp.yf0 = make_float2(q1.z, q1.w);
+                        pp.yf1 = make_float2(q2.x, q2.y);
+                        pp.yf2 = make_float2(q2.z, q2.w);
+                        pp.yla = yl.x;
+                        pp.ylb = yl.y;
+                        Cell ca, cb;
+                        if (yl.x != INT_MIN) {  // the same for every lane
+                            locate2<false>(X, nx, nxy, mx, my, mz, pp, nullptr, nullptr, ca, cb);
+                        } else {
+                            const int4 ya = sPyi[warp][j][0], yb = sPyi[warp][j][1];
+                            const int Ya[3] = {ya.x, ya.y, ya.z}, Yb[3] = {yb.x, yb.y, yb.z};
+                            locate2<true>(X, nx, nxy, mx, my, mz, pp, Ya, Yb, ca, cb);
+                        }
+                        gather<VARIANT, TS, true>(a, nx, nxy, ca, s, c);
+                        gather<VARIANT, TS, true>(a, nx, nxy, cb, s, c);
+                    }
                 }
                 __syncwarp();
                 if (lane < kc) {
