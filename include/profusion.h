@@ -76,9 +76,10 @@ typedef enum { PF_F32 = 0, PF_F16 = 1, PF_BF16 = 2, PF_FP8E4M3 = 3 } pf_dtype;
  * running-average weight; weight_u8 = 1 stores weights as uint8 (then
  * max_weight <= 255), 0 as float.
  * cell_view: the fitness reads a second copy of the grid in which the eight
- * corner values of every cell are contiguous (32 bytes per node, 16 for a
- * 16-bit grid, kept up to
- * date by fusion); 0 = when it needs at most 16 GiB, 1 = always, -1 = never. */
+ * corner values of every cell are contiguous (32 bytes per node; a 16-bit
+ * grid keeps a 16-byte record and a 32-byte float record per node, 48 bytes),
+ * kept up to date by fusion; 0 = when it needs at most 16 GiB, 1 = always,
+ * -1 = never. */
 typedef struct {
     int nx, ny, nz;
     float voxel_size;

@@ -105,6 +105,7 @@ struct pf_volume {
     void* tsdf = nullptr;      // encoded, see above; float, half or bfloat16 (desc.tsdf_dtype)
     void* weight = nullptr;    // float, or uint8 when desc.weight_u8
     void* cells = nullptr;     // cell view: 8 values per node (the cell whose lower corner it is)
+    float* cells32 = nullptr;  // 16-bit grids: the same view as float records (x-differences formed)
     int* tile_stamp = nullptr; // per fusion tile: stamp of the last fusion that reached it
     int stamp = 0;             // fusions so far
     int tiles[3] = {0, 0, 0};

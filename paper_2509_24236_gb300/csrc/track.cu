@@ -41,6 +41,7 @@
 #include <algorithm>
 #include <climits>
 #include <mutex>
+#include <type_traits>
 #include <vector>
 
 #include "pf_internal.cuh"
@@ -224,6 +225,7 @@ struct FitArgs {
     const void* tsdf;
     const void* weight;
     const void* cells;
+    const float* cells32; // 16-bit grids: the cell view as float records too
     int nx, ny, nz;
     double vs;
     double org[3];
@@ -517,12 +519,15 @@ __device__ __forceinline__ void load_cell(const __nv_bfloat16* cells, int idx, f
 // BRANCHLESS (cell view only): a sample outside the grid reads cell 0 and is
 // dropped by the final predicate instead of a branch -- cheaper when almost
 // every sample lands inside, as when particles share the lanes of a warp.
-template <int VARIANT, typename TS, bool BRANCHLESS = false>
+template <int VARIANT, typename TS, bool BRANCHLESS = false, bool FLOAT_CELLS = false>
 __device__ __forceinline__ void gather(const FitArgs& a, int nx, int nxy, const Cell& q, float& s, int& c)
 {
     if (VARIANT == 2 && BRANCHLESS) {
         float4 lo, hi;
-        load_cell(static_cast<const TS*>(a.cells), q.ok ? q.idx : 0, lo, hi);
+        if (FLOAT_CELLS)
+            load_cell(a.cells32, q.ok ? q.idx : 0, lo, hi);
+        else
+            load_cell(static_cast<const TS*>(a.cells), q.ok ? q.idx : 0, lo, hi);
         const float t = fabsf(trilerp_cell(q.fx, q.fy, q.fz, lo, hi));
         const bool use = q.ok && t < INFINITY;
         s += use ? t : 0.0f;
@@ -971,6 +976,9 @@ __device__ __forceinline__ void fitness_body(const FitArgs& a, int bx, int by, u
                     sPyi[warp][j][1] = make_int4(Yi[h + 2][0], Yi[h + 2][1], Yi[h + 2][2], 0);
                 }
                 __syncwarp();
+                // 16-bit grids: lanes on particles read the float records
+                // (no conversions; the same samples bit for bit)
+                constexpr bool kFloatCells = !std::is_same<TS, float>::value;
                 const int kl = lane < kc ? lane : 0;
                 XformD X;
                 load_xformd(sPD[kl], X);
@@ -993,8 +1001,8 @@ __device__ __forceinline__ void fitness_body(const FitArgs& a, int bx, int by, u
                         pp.ylb = yl.y;
                         Cell ca, cb;
                         locate2<false>(X, nx, nxy, mx, my, mz, pp, nullptr, nullptr, ca, cb);
-                        gather<VARIANT, TS, true>(a, nx, nxy, ca, s, c);
-                        gather<VARIANT, TS, true>(a, nx, nxy, cb, s, c);
+                        gather<VARIANT, TS, true, kFloatCells>(a, nx, nxy, ca, s, c);
+                        gather<VARIANT, TS, true, kFloatCells>(a, nx, nxy, cb, s, c);
                     }
                 } else {
 #pragma unroll 2
@@ -1018,8 +1026,8 @@ __device__ __forceinline__ void fitness_body(const FitArgs& a, int bx, int by, u
                             const int Ya[3] = {ya.x, ya.y, ya.z}, Yb[3] = {yb.x, yb.y, yb.z};
                             locate2<true>(X, nx, nxy, mx, my, mz, pp, Ya, Yb, ca, cb);
                         }
-                        gather<VARIANT, TS, true>(a, nx, nxy, ca, s, c);
-                        gather<VARIANT, TS, true>(a, nx, nxy, cb, s, c);
+                        gather<VARIANT, TS, true, kFloatCells>(a, nx, nxy, ca, s, c);
+                        gather<VARIANT, TS, true, kFloatCells>(a, nx, nxy, cb, s, c);
                     }
                 }
                 __syncwarp();
@@ -1359,6 +1367,7 @@ void fill_volume_args(FitArgs& a, const pf_volume* v)
     a.tsdf = v->tsdf;
     a.weight = v->weight;
     a.cells = v->cells;
+    a.cells32 = v->cells32;
     a.nx = v->desc.nx;
     a.ny = v->desc.ny;
     a.nz = v->desc.nz;

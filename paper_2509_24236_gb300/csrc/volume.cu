@@ -21,6 +21,8 @@
 #include <cstring>
 #include <vector>
 
+#include <type_traits>
+
 #include "pf_internal.cuh"
 
 namespace pf {
@@ -158,6 +160,7 @@ __global__ void fill_kernel(void* tsdf_, void* weight_, size_t n)
 struct RefreshArgs {
     const void* tsdf;
     void* cells;
+    float* cells32;  // 16-bit grids: the float records as well
     int nx, ny, nz;
     const int* tile_stamp;
     const int* stamp_dev;
@@ -185,6 +188,19 @@ __device__ inline void store_cell(const T* p, size_t nx, size_t nxy, T* cells, s
     reinterpret_cast<uint4*>(cells)[idx] = *reinterpret_cast<const uint4*>(h);
 }
 
+// The float record of a 16-bit grid: the stored values converted exactly and
+// the x-differences formed in float, as the 16-bit reader forms them, so both
+// records of a cell give bit-identical samples.
+template <typename T>
+__device__ inline void store_cell32(const T* p, size_t nx, size_t nxy, float* cells32, size_t idx)
+{
+    const float v000 = pf_to_float(p[0]), v010 = pf_to_float(p[nx]), v001 = pf_to_float(p[nxy]),
+                v011 = pf_to_float(p[nxy + nx]);
+    float4* c = reinterpret_cast<float4*>(cells32) + 2 * idx;
+    c[0] = make_float4(v000, pf_to_float(p[1]) - v000, v010, pf_to_float(p[nx + 1]) - v010);
+    c[1] = make_float4(v001, pf_to_float(p[nxy + 1]) - v001, v011, pf_to_float(p[nxy + nx + 1]) - v011);
+}
+
 template <typename TS>
 __global__ void __launch_bounds__(TX * TY, 4) cells_refresh_kernel(RefreshArgs a)
 {
@@ -210,6 +226,8 @@ __global__ void __launch_bounds__(TX * TY, 4) cells_refresh_kernel(RefreshArgs a
         if (k >= a.nz - 1) break;
         const size_t idx = i + nx * j + nxy * k;
         store_cell(tsdf + idx, nx, nxy, cells, idx);
+        if constexpr (!std::is_same<TS, float>::value)
+            if (a.cells32) store_cell32(tsdf + idx, nx, nxy, a.cells32, idx);
     }
 }
 
@@ -219,6 +237,7 @@ pf_status enqueue_refresh(pf_volume* v, cudaStream_t s, int all)
     RefreshArgs r;
     r.tsdf = v->tsdf;
     r.cells = v->cells;
+    r.cells32 = v->cells32;
     r.nx = v->desc.nx;
     r.ny = v->desc.ny;
     r.nz = v->desc.nz;
@@ -320,12 +339,17 @@ pf_status pf_create_volume(const pf_volume_desc* desc, void* stream, pf_volume**
     v->tiles[1] = (desc->ny + TY - 1) / TY;
     v->tiles[2] = (desc->nz + TZ - 1) / TZ;
     const size_t ts = pf_dtype_size(desc->tsdf_dtype), ws = desc->weight_u8 ? 1 : 4;
+    // a 16-bit grid keeps both its 16-bit records (lanes on points: two
+    // records per sector) and float records (lanes on particles: no
+    // conversions); a float grid has the float records only
+    const size_t bytes32 = desc->tsdf_dtype == PF_F32 ? 0 : v->n_nodes * 32;
     const size_t view_bytes = v->n_nodes * 8 * ts;
-    const bool view = desc->cell_view == 1 || (desc->cell_view == 0 && view_bytes <= (16ull << 30));
+    const bool view = desc->cell_view == 1 || (desc->cell_view == 0 && view_bytes + bytes32 <= (16ull << 30));
     cudaError_t e = cudaGetDevice(&v->device);
     if (e == cudaSuccess) e = cudaMalloc(&v->tsdf, v->n_nodes * ts);
     if (e == cudaSuccess) e = cudaMalloc(&v->weight, v->n_nodes * ws);
     if (e == cudaSuccess && view) e = cudaMalloc(&v->cells, view_bytes);
+    if (e == cudaSuccess && view && bytes32) e = cudaMalloc(&v->cells32, bytes32);
     if (e == cudaSuccess && view)
         e = cudaMalloc(&v->tile_stamp, sizeof(int) * ((size_t)v->tiles[0] * v->tiles[1] * v->tiles[2] + 1));
     if (e == cudaSuccess && view)
@@ -334,6 +358,7 @@ pf_status pf_create_volume(const pf_volume_desc* desc, void* stream, pf_volume**
         cudaFree(v->tsdf);
         cudaFree(v->weight);
         cudaFree(v->cells);
+        cudaFree(v->cells32);
         cudaFree(v->tile_stamp);
         delete v;
         cudaGetLastError();
@@ -356,6 +381,7 @@ pf_status pf_destroy_volume(pf_volume* v)
     cudaFree(v->tsdf);
     cudaFree(v->weight);
     cudaFree(v->cells);
+    cudaFree(v->cells32);
     cudaFree(v->tile_stamp);
     pf_workspace& w = v->ws;
     cudaFree(w.points);
