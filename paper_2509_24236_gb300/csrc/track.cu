@@ -726,7 +726,6 @@ __device__ __forceinline__ void fitness_body(const FitArgs& a, int bx, int by, u
     // of the warp): (x, y), (z, yf0), (yf1, yf2), and their reference cells
     __shared__ float4 sPair[FIT_WARPS][PPT * 16][3];
     __shared__ int2 sPyl[FIT_WARPS][PPT * 16];
-    __shared__ int4 sPyi[FIT_WARPS][PPT * 16][2];  // reference cells (x, y, z, -) of points a, b
     __shared__ float accS[FIT_WARPS][KC];
     __shared__ int accC[FIT_WARPS][KC];
     __shared__ int s_last;
@@ -972,8 +971,6 @@ __device__ __forceinline__ void fitness_body(const FitArgs& a, int bx, int by, u
                     sPair[warp][j][1] = make_float4(P2[h].z.x, P2[h].z.y, P2[h].yf0.x, P2[h].yf0.y);
                     sPair[warp][j][2] = make_float4(P2[h].yf1.x, P2[h].yf1.y, P2[h].yf2.x, P2[h].yf2.y);
                     sPyl[warp][j] = make_int2(P2[h].yla, P2[h].ylb);
-                    sPyi[warp][j][0] = make_int4(Yi[h][0], Yi[h][1], Yi[h][2], 0);
-                    sPyi[warp][j][1] = make_int4(Yi[h + 2][0], Yi[h + 2][1], Yi[h + 2][2], 0);
                 }
                 __syncwarp();
                 // 16-bit grids: lanes on particles read the float records
@@ -1022,8 +1019,12 @@ __device__ __forceinline__ void fitness_body(const FitArgs& a, int bx, int by, u
                         if (yl.x != INT_MIN) {  // the same for every lane
                             locate2<false>(X, nx, nxy, mx, my, mz, pp, nullptr, nullptr, ca, cb);
                         } else {
-                            const int4 ya = sPyi[warp][j][0], yb = sPyi[warp][j][1];
-                            const int Ya[3] = {ya.x, ya.y, ya.z}, Yb[3] = {yb.x, yb.y, yb.z};
+                            // a pair near the grid's edge (rare): the
+                            // reference cells again, from the points
+                            int Ya[3], Yb[3];
+                            float Fa[3], Fb[3];
+                            ref_apply(sRef, pp.x.x, pp.y.x, pp.z.x, Ya, Fa);
+                            ref_apply(sRef, pp.x.y, pp.y.y, pp.z.y, Yb, Fb);
                             locate2<true>(X, nx, nxy, mx, my, mz, pp, Ya, Yb, ca, cb);
                         }
                         gather<VARIANT, TS, true, kFloatCells>(a, nx, nxy, ca, s, c);
