@@ -1068,6 +1068,7 @@ __device__ __forceinline__ void fitness_body(const FitArgs& a, int bx, int by, u
         for (int k = tid; k < a.K; k += FIT_THREADS) {
             float S = 0.0f;
             int C = 0;
+#pragma unroll 4
             for (int y = 0; y < a.n_ptiles; ++y) {
                 S += __ldcg(a.part_S + (size_t)y * a.K + k);
                 C += __ldcg(a.part_C + (size_t)y * a.K + k);
@@ -1076,13 +1077,30 @@ __device__ __forceinline__ void fitness_body(const FitArgs& a, int bx, int by, u
             a.out_C[k] = C;
         }
     } else if (SRC == SRC_EVAL) {
+        // one pose over up to a few hundred tiles: every thread sums tiles
+        // tid, tid + 256, ... and the block combines the sums in a fixed order
+        __shared__ float s_eS[FIT_WARPS];
+        __shared__ int s_eC[FIT_WARPS];
+        float S = 0.0f;
+        int C = 0;
+        for (int y = tid; y < a.n_ptiles; y += FIT_THREADS) {
+            S += __ldcg(a.part_S + y);
+            C += __ldcg(a.part_C + y);
+        }
+        for (int o = 16; o > 0; o >>= 1) S += __shfl_xor_sync(0xffffffffu, S, o);
+        C = __reduce_add_sync(0xffffffffu, C);
+        if (lane == 0) {
+            s_eS[warp] = S;
+            s_eC[warp] = C;
+        }
+        __syncthreads();
         if (tid == 0) {
             if (!skip) {
-                float S = 0.0f;
-                int C = 0;
-                for (int y = 0; y < a.n_ptiles; ++y) {
-                    S += __ldcg(a.part_S + y);
-                    C += __ldcg(a.part_C + y);
+                S = 0.0f;
+                C = 0;
+                for (int w = 0; w < FIT_WARPS; ++w) {
+                    S += s_eS[w];
+                    C += s_eC[w];
                 }
                 const float E = C > 0 ? __fdiv_rn(S, (float)C) : INFINITY;
                 SearchState* st = a.st;
@@ -1121,6 +1139,7 @@ __device__ __forceinline__ void fitness_body(const FitArgs& a, int bx, int by, u
         for (int k = tid; k < a.K; k += FIT_THREADS) {
             float S = 0.0f;
             int C = 0;
+#pragma unroll 4
             for (int y = 0; y < a.n_ptiles; ++y) {
                 S += __ldcg(a.part_S + (size_t)y * a.K + k);
                 C += __ldcg(a.part_C + (size_t)y * a.K + k);
