@@ -6,8 +6,10 @@ compiled with gcc and called through ctypes.  Only the tests, the smoke check
 and the bench's CPU-baseline leg may use it; the CUDA library never does, and
 the two share no code.
 
-Parity pins for every function live in tests/test_oracle_pins.py; the oracle
-is pinned by closed forms and invariants, never by the CUDA path.
+Parity pins for every function live in tests/test_oracle_pins.py and (the
+alignment loss, its derivatives and the polish) tests/test_oracle_align.py;
+the oracle is pinned by closed forms, invariants and FP64 finite
+differences, never by the CUDA path.
 """
 from __future__ import annotations
 

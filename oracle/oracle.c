@@ -17,6 +17,10 @@
  *   defaults (Sec. IV-A): s^(1) = (10 deg, 10 cm), particle counts
  *     1024/3072/10240 and point down-sampling 1/8, 1/16, 1/32 alternating,
  *     at most 20 iterations.
+ *   gradient refinement (this project's addition on the residual of Sec.
+ *     III-B): the alignment loss sum tsdf(T x)^2, its derivatives with
+ *     respect to a left pose perturbation and to the node values, and a
+ *     damped Gauss-Newton polish of the pose.
  * Where the paper is silent the readings below are used (each is marked
  * "reading:" at its place): tsdf stored normalised by tau, trilinear lookup,
  * validity = all eight cell nodes observed with |tsdf| < 1, empty set -> E = +inf,
