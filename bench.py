@@ -61,6 +61,8 @@ def parse():
                          "paper: particles alternating 1024/3072/10240 with points decimated 1/8, 1/16, 1/32")
     ap.add_argument("--frame-step", type=int, default=1,
                     help="process every n-th frame of the trajectory (frames in between dropped)")
+    ap.add_argument("--polish", type=int, default=0,
+                    help="Gauss-Newton polish steps (pf_polish) after each frame's search, before fusion")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ref-particles", type=int, default=192,
@@ -289,6 +291,9 @@ def workload_config(args) -> dict:
     search = ("3072 particles x 20 iterations over all points" if not paper else
               "20 iterations, particles 1024/3072/10240 with points decimated 1/8, 1/16, 1/32 (paper schedule)")
     drop = "" if step == 1 else f", every {step}th frame (the others dropped)"
+    polish = getattr(args, "polish", 0)
+    if polish:
+        drop += f", {polish}-step Gauss-Newton polish after each search"
     k_sched, d_sched, _ = schedule(args)
     return {
         "workload": f"multiroom: 640x480 depth, 512^3 TSDF @ 1 cm (tau 3 cm, {storage_desc(args)}), "
@@ -353,9 +358,15 @@ def run_ours(args):
     stats_dev = torch.zeros((n_frames, stats_sz), dtype=torch.uint8, device=dev)
     pose_dev[0] = torch.from_numpy(gt[0].reshape(16)).to(dev)
 
+    polish_pts = torch.empty((intr.width * intr.height, 4), dtype=torch.float32, device=dev)
+    polish_n = torch.zeros(1, dtype=torch.int32, device=dev)
+
     def device_frame(f):
         pf.pf_pose_compose(pose_dev[f - 1], rel_dev[f], init_dev[f])
         vol.track_frame_async(depth_dev[f], intr, params, init_dev[f], pose_dev[f], stats_dev[f])
+        if args.polish > 0:
+            pf.pf_backproject(depth_dev[f], intr, polish_pts, polish_n)
+            vol.polish(polish_pts, pose_dev[f], steps=args.polish, n_dev=polish_n)
         vol.integrate_async(depth_dev[f], intr, pose_dev[f])
 
     # ---- device-resident pass -------------------------------------------
@@ -406,7 +417,7 @@ def run_ours(args):
 
     # ---- end-to-end pass through the host API ----------------------------
     e2e = None
-    if not args.no_e2e:
+    if not args.no_e2e and not args.polish:  # (the host-API pass has no polish step)
         e2e = run_e2e(pf, vol, gt, depths, rels, intr, params, W, K, dev)
 
     value = job_rate(K, world, ms_max)
