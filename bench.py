@@ -716,9 +716,11 @@ def run_batch(args):
     5.12 m scene, K = 1024 / 2048 / 3072 / 4096 by i % 4, 20 iterations over
     all points.  Frames 1..W+S of the multiroom trajectory (one rendering per
     camera size, shared by the sequences of that size); frame 0 is fused at
-    its true pose.  Times S steps of all sequences (a) one sequence after
-    another with pf_track_frame_async + pf_integrate_async, (b) as a batch
-    with direct launches, (c) as a batch replaying a CUDA graph.  Inputs are
+    its true pose.  Times S steps of all sequences (0) one sequence after
+    another with the plain float form (float volumes, fitness layout 1), (a)
+    one after another with the chosen storage and the default kernel
+    (pf_track_frame_async + pf_integrate_async), (b) as a batch with direct
+    launches, (c) as a batch replaying a CUDA graph.  Inputs are
     resident on the device.  Prints one JSON line (aggregate frames/s)."""
     import multiprocessing as mp
     W, S = max(1, args.warmup), max(1, args.steps)
@@ -760,24 +762,40 @@ def run_batch(args):
         torch.cuda.synchronize()
         return a.elapsed_time(b)
 
-    # (a) one sequence after another
-    for v in vols:
-        v.reserve(640 * 480, max(BATCH_K))
     pose = torch.zeros((BATCH_SEQS, n_frames, 16), dtype=torch.float64, device=dev)
     init = torch.zeros_like(pose)
-    for i, (r, seq) in enumerate(seqs):
-        pose[i, 0] = torch.from_numpy(seq.gt[0].reshape(16)).to(dev)
-        vols[i].integrate_async(depth[r, 0], seq.intr, pose[i, 0])
 
-    def seq_frames(f0, f1):
-        for f in range(f0, f1):
-            for i, (r, seq) in enumerate(seqs):
-                pf.pf_pose_compose(pose[i, f - 1], rels[i][f], init[i, f])
-                vols[i].track_frame_async(depth[r, f], seq.intr, params[i], init[i, f], pose[i, f])
-                vols[i].integrate_async(depth[r, f], seq.intr, pose[i, f])
+    def sequential(vs):
+        """Frames 1..W warm-up, then S timed frames of every sequence, one
+        sequence after another (pf_track_frame_async + pf_integrate_async)."""
+        for v in vs:
+            v.reserve(640 * 480, max(BATCH_K))
+        for i, (r, seq) in enumerate(seqs):
+            pose[i, 0] = torch.from_numpy(seq.gt[0].reshape(16)).to(dev)
+            vs[i].integrate_async(depth[r, 0], seq.intr, pose[i, 0])
 
-    seq_frames(1, W + 1)
-    ms_seq = timed(lambda: seq_frames(W + 1, W + S + 1))
+        def frames(f0, f1):
+            for f in range(f0, f1):
+                for i, (r, seq) in enumerate(seqs):
+                    pf.pf_pose_compose(pose[i, f - 1], rels[i][f], init[i, f])
+                    vs[i].track_frame_async(depth[r, f], seq.intr, params[i], init[i, f], pose[i, f])
+                    vs[i].integrate_async(depth[r, f], seq.intr, pose[i, f])
+
+        frames(1, W + 1)
+        return timed(lambda: frames(W + 1, W + S + 1))
+
+    # (0) the plain float form (float storage, fitness layout 1), one after another
+    plain = []
+    for _, seq in seqs:
+        v = pf.Volume.from_grid(seq.grid)
+        v.set_fitness_variant(1)
+        plain.append(v)
+    ms_plain = sequential(plain)
+    for v in plain:
+        v.close()
+    del plain
+    # (a) this storage and the default kernel, one after another
+    ms_seq = sequential(vols)
     pose_seq = pose.cpu().numpy()
 
     # (b), (c) batches, from the same start
@@ -815,10 +833,12 @@ def run_batch(args):
         "kernel": "batch", "sequences": BATCH_SEQS, "steps": S, "warmup": W, "storage": storage_desc(args),
         "mix": "cameras 160x120/320x240/640x480 by i%3, volumes 128^3/256^3/384^3 over 5.12 m by (i//3)%3, "
                "K 1024/2048/3072/4096 by i%4, 20 iterations, all points",
+        "frames_per_s_plain_f32_sequential": frames / (ms_plain / 1e3),
         "frames_per_s_sequential": frames / (ms_seq / 1e3),
         "frames_per_s_batch_direct": frames / (out["direct"] / 1e3),
         "frames_per_s_batch_graph": frames / (out["graph"] / 1e3),
         "speedup_graph_vs_sequential": ms_seq / out["graph"],
+        "speedup_graph_vs_plain_f32_sequential": ms_plain / out["graph"],
         "points_per_block": out.get("points_per_block"),
         "max_final_position_difference_batch_vs_sequential_m": out["pose_diff_m"],
     }))
