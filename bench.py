@@ -53,9 +53,12 @@ def parse():
     ap.add_argument("--update-mode", type=int, default=0)
     ap.add_argument("--compose-mode", type=int, default=1)
     ap.add_argument("--seed", type=int, default=0)
-    ap.add_argument("--tsdf-dtype", default="f32", choices=["f32", "f16", "bf16"],
-                    help="storage type of the TSDF and its cell view (arithmetic stays f32)")
+    ap.add_argument("--tsdf-dtype", default="f32", choices=["f32", "f16", "bf16", "fp8"],
+                    help="storage type of the TSDF and its cell view (arithmetic stays f32); "
+                         "fp8 = e4m3 holding 256 x the value")
     ap.add_argument("--weight-u8", action="store_true", help="store fusion weights as uint8")
+    ap.add_argument("--cell-view", type=int, default=0, choices=[-1, 0, 1, 2],
+                    help="cell view of the volumes: 0 automatic, 1 full, 2 narrow records only, -1 none")
     ap.add_argument("--schedule", default="fixed", choices=["fixed", "paper"],
                     help="fixed: 3072 particles x 20 iterations over all points (the benchmark configuration); "
                          "paper: particles alternating 1024/3072/10240 with points decimated 1/8, 1/16, 1/32")
@@ -270,12 +273,14 @@ def run_reference(args):
 
 
 def storage_desc(args) -> str:
-    return f"{getattr(args, 'tsdf_dtype', 'f32')} tsdf + {'u8' if getattr(args, 'weight_u8', False) else 'f32'} weight"
+    view = {0: "", 1: ", full cell view", 2: ", narrow cell view", -1: ", no cell view"}[int(getattr(args, "cell_view", 0))]
+    return f"{getattr(args, 'tsdf_dtype', 'f32')} tsdf + {'u8' if getattr(args, 'weight_u8', False) else 'f32'} weight{view}"
 
 
 def new_volume(pf, grid, args):
-    dt = {"f32": pf.PF_F32, "f16": pf.PF_F16, "bf16": pf.PF_BF16}[args.tsdf_dtype]
-    return pf.Volume.from_grid(grid, tsdf_dtype=dt, weight_u8=int(args.weight_u8))
+    dt = {"f32": pf.PF_F32, "f16": pf.PF_F16, "bf16": pf.PF_BF16, "fp8": pf.PF_FP8E4M3}[args.tsdf_dtype]
+    return pf.Volume.from_grid(grid, tsdf_dtype=dt, weight_u8=int(args.weight_u8),
+                               cell_view=int(getattr(args, "cell_view", 0)))
 
 
 def schedule(args):
@@ -924,11 +929,13 @@ def run_room64(args):
 def run_precision(args):
     """Reduced-precision storage at scale: the multiroom trajectory (frames
     0..--steps) at 640x480 into a 768^3 TSDF at 8 mm (tau 2.4 cm), tsdf in
-    f32 / f16 / bf16 with uint8 weights.  (a) Fusion of every frame at its
-    true pose: RMS and max deviation of the 16-bit volumes from the f32 one
-    over nodes observed in both (the f32 fusion matches the FP64 oracle to
-    1e-5, see the parity tests).  (b) Tracking + fusion of the same frames:
-    frames/s (CUDA events), ATE and the largest distance between each
+    f32 / f16 / bf16 / scaled e4m3 with uint8 weights; the narrow storages
+    with the automatic (full) cell view and with the narrow one.  Per run:
+    the view taken and the device bytes per node.  (a) Fusion of every frame
+    at its true pose: RMS and max deviation of the narrow volumes from the
+    f32 one over nodes observed in both (the f32 fusion matches the FP64
+    oracle to 1e-5, see the parity tests).  (b) Tracking + fusion of the same
+    frames: frames/s (CUDA events), ATE and the largest distance between each
     trajectory and the f32 one."""
     import synth
     n = max(2, args.steps + 1)
@@ -949,18 +956,20 @@ def run_precision(args):
     dev = torch.device("cuda", 0)
     intr = seq.intr
     dd = [torch.from_numpy(d).to(dev) for d in depths]
-    codes = {"f32": pf.PF_F32, "f16": pf.PF_F16, "bf16": pf.PF_BF16}
+    codes = {"f32": pf.PF_F32, "f16": pf.PF_F16, "bf16": pf.PF_BF16, "fp8": pf.PF_FP8E4M3}
     templ = torch.from_numpy(synth.templates(K_PARTICLES, args.seed)).to(dev)
     params = pf.track_params(templ, n_iters=N_ITERS, k_sched=(K_PARTICLES,) * 3, decim_sched=(1, 1, 1),
                              update_mode=args.update_mode, compose_mode=args.compose_mode, min_valid_frac=0.05)
     rel_dev = torch.from_numpy(np.stack([r.reshape(16) for r in rels])).to(dev)
     res, ref_tsdf, ref_w, ref_traj = {}, None, None, None
-    for name in ("f32", "f16", "bf16"):
-        vol = pf.Volume.from_grid(grid, tsdf_dtype=codes[name], weight_u8=1)
+    for name, view in (("f32", 0), ("f16", 0), ("f16", 2), ("bf16", 0), ("bf16", 2), ("fp8", 0), ("fp8", 2)):
+        vol = pf.Volume.from_grid(grid, tsdf_dtype=codes[name], weight_u8=1, cell_view=view)
+        info = vol.info()
         for f in range(n):
             vol.integrate(dd[f], intr, seq.gt[f])
         t, w = vol.download()
-        r = {}
+        r = {"cell_view": {1: "full", 2: "narrow", -1: "none"}[info["cell_view"]],
+             "storage_bytes_per_node": info["storage_bytes"] / grid.n_nodes}
         if ref_tsdf is None:
             ref_tsdf, ref_w = t, w
         else:
@@ -993,7 +1002,7 @@ def run_precision(args):
         else:
             r["max_position_difference_to_f32_cm"] = 100 * float(np.max(np.linalg.norm(P[1:, :3, 3] - ref_traj[1:, :3, 3],
                                                                                        axis=1)))
-        res[name + "+u8"] = r
+        res[name + "+u8" + ("+narrow" if view == 2 else "")] = r
         vol.close()
     print(json.dumps({"kernel": "precision", "workload": f"multiroom 640x480, {n - 1} tracked frames, 768^3 TSDF @ "
                       "8 mm (tau 2.4 cm), 3072 particles x 20 iterations, uint8 weights", "results": res}))

@@ -62,12 +62,15 @@ typedef struct {
     float depth_min, depth_max;
 } pf_intrinsics;
 
-/* Storage type of the TSDF values (and of the cell view).  PF_F32, PF_F16
- * and PF_BF16 are supported; PF_FP8E4M3 is rejected with PF_ERR_UNSUPPORTED.
- * A 16-bit grid stores the value rounded to nearest; a value that rounds to
- * +-1 is stored as the outside-the-band code (+-1 exactly), so the fitness
- * treats such a node as outside the band.  All arithmetic (fusion average,
- * trilinear sample, sums) is float; only the stored values are rounded. */
+/* Storage type of the TSDF values (and of the cell view): PF_F32, PF_F16,
+ * PF_BF16, or PF_FP8E4M3 -- e4m3 holding the value times 256 (3 mantissa
+ * bits; the scale keeps values near the surface out of the e4m3
+ * subnormals), with the largest code +-448 standing for the outside-the-band
+ * +-1 and the NaN code for unobserved.  Values are rounded to nearest; a
+ * value that rounds to +-1 is stored as the outside-the-band code, so the
+ * fitness treats such a node as outside the band.  All arithmetic (fusion
+ * average, trilinear sample, sums) is float; only the stored values are
+ * rounded.  Other codes are rejected with PF_ERR_UNSUPPORTED. */
 typedef enum { PF_F32 = 0, PF_F16 = 1, PF_BF16 = 2, PF_FP8E4M3 = 3 } pf_dtype;
 
 /* Dense TSDF grid (Sec. III: "a tensor that records the distance value in
@@ -76,10 +79,16 @@ typedef enum { PF_F32 = 0, PF_F16 = 1, PF_BF16 = 2, PF_FP8E4M3 = 3 } pf_dtype;
  * running-average weight; weight_u8 = 1 stores weights as uint8 (then
  * max_weight <= 255), 0 as float.
  * cell_view: the fitness reads a second copy of the grid in which the eight
- * corner values of every cell are contiguous (32 bytes per node; a 16-bit
- * grid keeps a 16-byte record and a 32-byte float record per node, 48 bytes),
- * kept up to date by fusion; 0 = when it needs at most 16 GiB, 1 = always,
- * -1 = never. */
+ * corner values of every cell are contiguous, kept up to date by fusion.
+ * A float grid's records are 32 bytes per node.  The full view of a 16-bit
+ * (8-bit) grid keeps a 16-byte (8-byte) record and a 32-byte float record
+ * per node; its narrow view keeps the 16-byte (8-byte) record only (lanes
+ * on particles then convert on load).  -1 = no view; 1 = the full view;
+ * 2 = the narrow view (a float grid takes 1); 0 = automatic: the full
+ * view when the whole volume (grid, weights, view) fits in half of the
+ * device memory free at creation (decoding narrow records on load slows the
+ * search once the particles converge), else the narrow view when that
+ * fits, else none.  pf_volume_info reports the choice. */
 typedef struct {
     int nx, ny, nz;
     float voxel_size;
@@ -374,6 +383,12 @@ PF_API pf_status pf_polish(const pf_volume* vol, const float* points_dev, const 
  * (instead of forming it from exact reference products), so its values
  * differ from the others by that rounding. */
 PF_API pf_status pf_set_fitness_variant(pf_volume* vol, int variant);
+
+/* Device memory a volume holds for its grid, weights and cell view
+ * (workspaces of the search excluded) in *storage_bytes, and the cell view
+ * it took in *cell_view (-1 none, 1 full, 2 narrow; see pf_volume_desc).
+ * Either pointer may be NULL.  PF_ERR_INVALID_ARG for a NULL volume. */
+PF_API pf_status pf_volume_info(const pf_volume* vol, unsigned long long* storage_bytes, int* cell_view);
 
 PF_API const char* pf_status_string(pf_status status);
 

@@ -66,7 +66,7 @@ EXPORTS = ["pf_create_volume", "pf_destroy_volume", "pf_reset_volume", "pf_volum
            "pf_track_reserve", "pf_raycast", "pf_set_fitness_variant", "pf_status_string", "pf_launch_count",
            "pf_set_kernel_timing", "pf_kernel_timing", "pf_align_loss", "pf_polish",
            "pf_batch_create", "pf_batch_destroy", "pf_batch_buffers", "pf_batch_fuse", "pf_batch_step",
-           "pf_batch_autotune", "pf_batch_set_points_per_block"]
+           "pf_batch_autotune", "pf_batch_set_points_per_block", "pf_volume_info"]
 
 _lib = None
 
@@ -107,6 +107,7 @@ def load(path: str = LIB_PATH):
         "pf_track_reserve": (st, [vp, C.c_int, C.c_int]),
         "pf_raycast": (st, [vp, C.POINTER(pf_intrinsics), dp, vp, vp, vp]),
         "pf_set_fitness_variant": (st, [vp, C.c_int]),
+        "pf_volume_info": (st, [vp, C.POINTER(C.c_ulonglong), C.POINTER(C.c_int)]),
         "pf_status_string": (C.c_char_p, [st]),
         "pf_launch_count": (C.c_ulonglong, []),
         "pf_set_kernel_timing": (st, [C.c_int]),
@@ -306,6 +307,13 @@ def pf_set_fitness_variant(vol, variant: int) -> int:
     return _check(load().pf_set_fitness_variant(vol, int(variant)), "pf_set_fitness_variant")
 
 
+def pf_volume_info(vol):
+    """(storage bytes, cell view) of a volume: -1 no view, 1 full, 2 narrow."""
+    b, m = C.c_ulonglong(0), C.c_int(0)
+    _check(load().pf_volume_info(vol, C.byref(b), C.byref(m)), "pf_volume_info")
+    return int(b.value), int(m.value)
+
+
 def pf_launch_count() -> int:
     return int(load().pf_launch_count())
 
@@ -399,6 +407,10 @@ class Volume:
 
     def set_fitness_variant(self, variant: int):
         pf_set_fitness_variant(self.handle, variant)
+
+    def info(self) -> dict:
+        b, m = pf_volume_info(self.handle)
+        return {"storage_bytes": b, "cell_view": m}
 
     def align_loss(self, points, poses, counts=None, xi=None, dloss=None, grad_xi=False, grad_tsdf=False,
                    stream=None):

@@ -579,6 +579,7 @@ void launch_storage(const pf_volume* v, dim3 grid, cudaStream_t s, const Args& a
     switch (v->desc.tsdf_dtype) {
     case PF_F16: K<__half>::run(grid, s, a); break;
     case PF_BF16: K<__nv_bfloat16>::run(grid, s, a); break;
+    case PF_FP8E4M3: K<__nv_fp8_e4m3>::run(grid, s, a); break;
     default: K<float>::run(grid, s, a); break;
     }
 }

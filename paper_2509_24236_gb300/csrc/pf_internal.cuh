@@ -3,6 +3,7 @@
 
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
+#include <cuda_fp8.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -48,16 +49,33 @@ __host__ __device__ inline float pf_decode(float e)
 }
 
 // --------------------------------------------------------------------------
-// Storage types.  The tsdf (and the cell view) are stored as float, half or
-// bfloat16 -- the encoding above survives the conversion (NaN and infinities
-// are kept) and a value that rounds to +-1 is stored as +-infinity, so a
-// finite stored value always lies inside the band -- and the weight as float
-// or uint8.  All arithmetic is float.
+// Storage types.  The tsdf (and the cell view) are stored as float, half,
+// bfloat16 or scaled e4m3 -- the encoding above survives the conversion
+// (NaN and infinities are kept; e4m3 codes them as below) and a value that
+// rounds to +-1 is stored as +-infinity, so a finite stored value always
+// lies inside the band -- and the weight as float or uint8.  All arithmetic
+// is float.
 // --------------------------------------------------------------------------
 __host__ __device__ inline float pf_to_float(float v) { return v; }
 __host__ __device__ inline float pf_to_float(__half v) { return __half2float(v); }
 __host__ __device__ inline float pf_to_float(__nv_bfloat16 v) { return __bfloat162float(v); }
 __host__ __device__ inline float pf_to_float(uint8_t v) { return (float)v; }
+
+// 8-bit storage (PF_FP8E4M3): the value scaled by 2^8 in e4m3 (a value in
+// (-1, 1) keeps 3 mantissa bits; the scale lifts the values near the surface
+// out of the e4m3 subnormals).  e4m3 has no infinities: the largest finite
+// code, +-448, stands for the outside-the-band +-1 and the NaN code for
+// unobserved.  Scaled values stay below 256 in magnitude, so 448 never
+// collides with a value.
+constexpr float PF_FP8_SCALE = 256.0f;
+constexpr unsigned char PF_FP8_NAN = 0x7f, PF_FP8_POS = 0x7e, PF_FP8_NEG = 0xfe;
+__host__ __device__ inline float pf_to_float(__nv_fp8_e4m3 v)
+{
+    const __half h(__nv_cvt_fp8_to_halfraw(v.__x, __NV_E4M3));
+    const float f = __half2float(h);
+    if (f != f) return f;
+    return fabsf(f) >= 448.0f ? copysignf(INFINITY, f) : f * (1.0f / PF_FP8_SCALE);
+}
 
 template <typename T> __host__ __device__ inline T pf_from_float(float v);
 template <> __host__ __device__ inline float pf_from_float<float>(float v) { return v; }
@@ -72,8 +90,23 @@ template <> __host__ __device__ inline __nv_bfloat16 pf_from_float<__nv_bfloat16
     return __float2bfloat16_rn(r >= 1.0f ? INFINITY : (r <= -1.0f ? -INFINITY : v));
 }
 template <> __host__ __device__ inline uint8_t pf_from_float<uint8_t>(float v) { return (uint8_t)v; }
+template <> __host__ __device__ inline __nv_fp8_e4m3 pf_from_float<__nv_fp8_e4m3>(float v)
+{
+    __nv_fp8_e4m3 r;
+    if (v != v) {
+        r.__x = PF_FP8_NAN;
+    } else if (v >= 1.0f || v <= -1.0f) {
+        r.__x = v > 0.0f ? PF_FP8_POS : PF_FP8_NEG;
+    } else {
+        r.__x = __nv_cvt_float_to_fp8(v * PF_FP8_SCALE, __NV_SATFINITE, __NV_E4M3);
+        const float back = __half2float(__half(__nv_cvt_fp8_to_halfraw(r.__x, __NV_E4M3)));
+        if (back >= PF_FP8_SCALE) r.__x = PF_FP8_POS;       // rounds to +-1: outside the band
+        else if (back <= -PF_FP8_SCALE) r.__x = PF_FP8_NEG;
+    }
+    return r;
+}
 
-inline size_t pf_dtype_size(pf_dtype t) { return t == PF_F32 ? 4 : 2; }
+inline size_t pf_dtype_size(pf_dtype t) { return t == PF_F32 ? 4 : t == PF_FP8E4M3 ? 1 : 2; }
 
 // --------------------------------------------------------------------------
 // Volume and workspace
@@ -105,7 +138,7 @@ struct pf_volume {
     void* tsdf = nullptr;      // encoded, see above; float, half or bfloat16 (desc.tsdf_dtype)
     void* weight = nullptr;    // float, or uint8 when desc.weight_u8
     void* cells = nullptr;     // cell view: 8 values per node (the cell whose lower corner it is)
-    float* cells32 = nullptr;  // 16-bit grids: the same view as float records (x-differences formed)
+    float* cells32 = nullptr;  // 16-/8-bit grids, full view: the same records as floats (x-differences formed)
     int* tile_stamp = nullptr; // per fusion tile: stamp of the last fusion that reached it
     int stamp = 0;             // fusions so far
     int tiles[3] = {0, 0, 0};

@@ -148,6 +148,8 @@ extern "C" pf_status pf_raycast(const pf_volume* v, const pf_intrinsics* intr, c
         raycast_kernel<__half><<<grid, block, 0, s>>>(a);
     else if (v->desc.tsdf_dtype == PF_BF16)
         raycast_kernel<__nv_bfloat16><<<grid, block, 0, s>>>(a);
+    else if (v->desc.tsdf_dtype == PF_FP8E4M3)
+        raycast_kernel<__nv_fp8_e4m3><<<grid, block, 0, s>>>(a);
     else
         raycast_kernel<float><<<grid, block, 0, s>>>(a);
     pf::count_launch();

@@ -225,7 +225,7 @@ struct FitArgs {
     const void* tsdf;
     const void* weight;
     const void* cells;
-    const float* cells32; // 16-bit grids: the cell view as float records too
+    const float* cells32; // 16-/8-bit grids, full view: the records as floats too (else null)
     int nx, ny, nz;
     double vs;
     double org[3];
@@ -503,6 +503,34 @@ __device__ __forceinline__ void load_cell(const __half* cells, int idx, float4& 
     corners_to_cell(a.x, a.y, b.x, b.y, c.x, c.y, d.x, d.y, lo, hi);
 }
 
+// Scaled e4m3 records: one 8-byte load; each pair of codes goes to half2 in
+// one conversion and is multiplied by 160 in half, which is exact (3 + 3
+// significant bits) for every value code and overflows the outside-the-band
+// code 448 to infinity (448 x 160 > 65504 > 240 x 160), so the float record
+// below holds 160 x 256 = 40960 times the stored values, with the band's
+// edge non-finite as in the other layouts; the interpolated value is scaled
+// back once (cell_scale).
+__device__ __forceinline__ void load_cell(const __nv_fp8_e4m3* cells, int idx, float4& lo, float4& hi)
+{
+    const uint2 r = __ldg(reinterpret_cast<const uint2*>(cells) + idx);
+    const __half2 k = __floats2half2_rn(160.0f, 160.0f);
+    float2 q[4];
+    const unsigned short pairs[4] = {(unsigned short)(r.x & 0xffffu), (unsigned short)(r.x >> 16),
+                                     (unsigned short)(r.y & 0xffffu), (unsigned short)(r.y >> 16)};
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const __half2 h(__nv_cvt_fp8x2_to_halfraw2(pairs[i], __NV_E4M3));
+        q[i] = __half22float2(__hmul2(h, k));
+    }
+    corners_to_cell(q[0].x, q[0].y, q[1].x, q[1].y, q[2].x, q[2].y, q[3].x, q[3].y, lo, hi);
+}
+
+template <typename T>
+__device__ __forceinline__ constexpr float cell_scale()
+{
+    return std::is_same<T, __nv_fp8_e4m3>::value ? 1.0f / (160.0f * PF_FP8_SCALE) : 1.0f;
+}
+
 __device__ __forceinline__ void load_cell(const __nv_bfloat16* cells, int idx, float4& lo, float4& hi)
 {
     // a bfloat16 is the upper half of a float
@@ -528,7 +556,8 @@ __device__ __forceinline__ void gather(const FitArgs& a, int nx, int nxy, const 
             load_cell(a.cells32, q.ok ? q.idx : 0, lo, hi);
         else
             load_cell(static_cast<const TS*>(a.cells), q.ok ? q.idx : 0, lo, hi);
-        const float t = fabsf(trilerp_cell(q.fx, q.fy, q.fz, lo, hi));
+        constexpr float k = FLOAT_CELLS ? 1.0f : cell_scale<TS>();
+        const float t = fabsf(trilerp_cell(q.fx, q.fy, q.fz, lo, hi)) * k;
         const bool use = q.ok && t < INFINITY;
         s += use ? t : 0.0f;
         c += use ? 1 : 0;
@@ -538,7 +567,7 @@ __device__ __forceinline__ void gather(const FitArgs& a, int nx, int nxy, const 
     if (VARIANT == 2) {
         float4 lo, hi;
         load_cell(static_cast<const TS*>(a.cells), q.idx, lo, hi);
-        accumulate(trilerp_cell(q.fx, q.fy, q.fz, lo, hi), s, c);
+        accumulate(trilerp_cell(q.fx, q.fy, q.fz, lo, hi) * cell_scale<TS>(), s, c);
     } else if (VARIANT == 0) {
         const TS* p = static_cast<const TS*>(a.tsdf) + q.idx;
         accumulate(trilerp(q.fx, q.fy, q.fz, pf_to_float(p[0]), pf_to_float(p[1]), pf_to_float(p[nx]),
@@ -973,63 +1002,76 @@ __device__ __forceinline__ void fitness_body(const FitArgs& a, int bx, int by, u
                     sPyl[warp][j] = make_int2(P2[h].yla, P2[h].ylb);
                 }
                 __syncwarp();
-                // 16-bit grids: lanes on particles read the float records
-                // (no conversions; the same samples bit for bit)
-                constexpr bool kFloatCells = !std::is_same<TS, float>::value;
                 const int kl = lane < kc ? lane : 0;
                 XformD X;
                 load_xformd(sPD[kl], X);
                 float s = 0.0f;
                 int c = 0;
-                if (__all_sync(0xffffffffu, in_all)) {
-                    // every pair of the warp is interior: no range tests
+                // 16-/8-bit grids: lanes on particles read the float records
+                // of a full view (no conversions; for 16-bit storage the
+                // same samples bit for bit), else the narrow records; the
+                // loops are instantiated once per source so that the choice
+                // costs the inner loop nothing
+                auto pair_loops = [&](auto float_cells) {
+                    constexpr bool FC = decltype(float_cells)::value;
+                    if (__all_sync(0xffffffffu, in_all)) {
+                        // every pair of the warp is interior: no range tests
 #pragma unroll 4
-                    for (int j = 0; j < PPT * 16; ++j) {
-                        const float4 q0 = sPair[warp][j][0], q1 = sPair[warp][j][1], q2 = sPair[warp][j][2];
-                        const int2 yl = sPyl[warp][j];
-                        PointPair pp;
-                        pp.x = make_float2(q0.x, q0.y);
-                        pp.y = make_float2(q0.z, q0.w);
-                        pp.z = make_float2(q1.x, q1.y);
-                        pp.yf0 = make_float2(q1.z, q1.w);
-                        pp.yf1 = make_float2(q2.x, q2.y);
-                        pp.yf2 = make_float2(q2.z, q2.w);
-                        pp.yla = yl.x;
-                        pp.ylb = yl.y;
-                        Cell ca, cb;
-                        locate2<false>(X, nx, nxy, mx, my, mz, pp, nullptr, nullptr, ca, cb);
-                        gather<VARIANT, TS, true, kFloatCells>(a, nx, nxy, ca, s, c);
-                        gather<VARIANT, TS, true, kFloatCells>(a, nx, nxy, cb, s, c);
-                    }
-                } else {
-#pragma unroll 2
-                    for (int j = 0; j < PPT * 16; ++j) {
-                        const float4 q0 = sPair[warp][j][0], q1 = sPair[warp][j][1], q2 = sPair[warp][j][2];
-                        const int2 yl = sPyl[warp][j];
-                        PointPair pp;
-                        pp.x = make_float2(q0.x, q0.y);
-                        pp.y = make_float2(q0.z, q0.w);
-                        pp.z = make_float2(q1.x, q1.y);
-                        pp.yf0 = make_float2(q1.z, q1.w);
-                        pp.yf1 = make_float2(q2.x, q2.y);
-                        pp.yf2 = make_float2(q2.z, q2.w);
-                        pp.yla = yl.x;
-                        pp.ylb = yl.y;
-                        Cell ca, cb;
-                        if (yl.x != INT_MIN) {  // the same for every lane
+                        for (int j = 0; j < PPT * 16; ++j) {
+                            const float4 q0 = sPair[warp][j][0], q1 = sPair[warp][j][1], q2 = sPair[warp][j][2];
+                            const int2 yl = sPyl[warp][j];
+                            PointPair pp;
+                            pp.x = make_float2(q0.x, q0.y);
+                            pp.y = make_float2(q0.z, q0.w);
+                            pp.z = make_float2(q1.x, q1.y);
+                            pp.yf0 = make_float2(q1.z, q1.w);
+                            pp.yf1 = make_float2(q2.x, q2.y);
+                            pp.yf2 = make_float2(q2.z, q2.w);
+                            pp.yla = yl.x;
+                            pp.ylb = yl.y;
+                            Cell ca, cb;
                             locate2<false>(X, nx, nxy, mx, my, mz, pp, nullptr, nullptr, ca, cb);
-                        } else {
-                            // a pair near the grid's edge (rare): the
-                            // reference cells again, from the points
-                            int Ya[3], Yb[3];
-                            float Fa[3], Fb[3];
-                            ref_apply(sRef, pp.x.x, pp.y.x, pp.z.x, Ya, Fa);
-                            ref_apply(sRef, pp.x.y, pp.y.y, pp.z.y, Yb, Fb);
-                            locate2<true>(X, nx, nxy, mx, my, mz, pp, Ya, Yb, ca, cb);
+                            gather<VARIANT, TS, true, FC>(a, nx, nxy, ca, s, c);
+                            gather<VARIANT, TS, true, FC>(a, nx, nxy, cb, s, c);
                         }
-                        gather<VARIANT, TS, true, kFloatCells>(a, nx, nxy, ca, s, c);
-                        gather<VARIANT, TS, true, kFloatCells>(a, nx, nxy, cb, s, c);
+                    } else {
+#pragma unroll 2
+                        for (int j = 0; j < PPT * 16; ++j) {
+                            const float4 q0 = sPair[warp][j][0], q1 = sPair[warp][j][1], q2 = sPair[warp][j][2];
+                            const int2 yl = sPyl[warp][j];
+                            PointPair pp;
+                            pp.x = make_float2(q0.x, q0.y);
+                            pp.y = make_float2(q0.z, q0.w);
+                            pp.z = make_float2(q1.x, q1.y);
+                            pp.yf0 = make_float2(q1.z, q1.w);
+                            pp.yf1 = make_float2(q2.x, q2.y);
+                            pp.yf2 = make_float2(q2.z, q2.w);
+                            pp.yla = yl.x;
+                            pp.ylb = yl.y;
+                            Cell ca, cb;
+                            if (yl.x != INT_MIN) {  // the same for every lane
+                                locate2<false>(X, nx, nxy, mx, my, mz, pp, nullptr, nullptr, ca, cb);
+                            } else {
+                                // a pair near the grid's edge (rare): the
+                                // reference cells again, from the points
+                                int Ya[3], Yb[3];
+                                float Fa[3], Fb[3];
+                                ref_apply(sRef, pp.x.x, pp.y.x, pp.z.x, Ya, Fa);
+                                ref_apply(sRef, pp.x.y, pp.y.y, pp.z.y, Yb, Fb);
+                                locate2<true>(X, nx, nxy, mx, my, mz, pp, Ya, Yb, ca, cb);
+                            }
+                            gather<VARIANT, TS, true, FC>(a, nx, nxy, ca, s, c);
+                            gather<VARIANT, TS, true, FC>(a, nx, nxy, cb, s, c);
+                        }
                     }
+                };
+                if constexpr (!std::is_same<TS, float>::value) {
+                    if (a.cells32 != nullptr)
+                        pair_loops(std::true_type{});
+                    else
+                        pair_loops(std::false_type{});
+                } else {
+                    pair_loops(std::false_type{});
                 }
                 __syncwarp();
                 if (lane < kc) {
@@ -1377,6 +1419,8 @@ void launch_fitness(FitArgs a, int variant, const pf_volume* v, int chunks, cuda
         launch_fitness_t<SRC, __half>(a, layout, grid, s);
     else if (v->desc.tsdf_dtype == PF_BF16)
         launch_fitness_t<SRC, __nv_bfloat16>(a, layout, grid, s);
+    else if (v->desc.tsdf_dtype == PF_FP8E4M3)
+        launch_fitness_t<SRC, __nv_fp8_e4m3>(a, layout, grid, s);
     else
         launch_fitness_t<SRC, float>(a, layout, grid, s);
     pf::count_launch();
@@ -1828,6 +1872,8 @@ void launch_batch(const pf_batch* b, int it, int kind, cudaStream_t s)
         launch_batch_t<SRC, __half>(b, args, first, n, blocks, s);
     else if (b->dtype == PF_BF16)
         launch_batch_t<SRC, __nv_bfloat16>(b, args, first, n, blocks, s);
+    else if (b->dtype == PF_FP8E4M3)
+        launch_batch_t<SRC, __nv_fp8_e4m3>(b, args, first, n, blocks, s);
     else
         launch_batch_t<SRC, float>(b, args, first, n, blocks, s);
     pf::count_launch();

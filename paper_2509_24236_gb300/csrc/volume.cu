@@ -160,7 +160,7 @@ __global__ void fill_kernel(void* tsdf_, void* weight_, size_t n)
 struct RefreshArgs {
     const void* tsdf;
     void* cells;
-    float* cells32;  // 16-bit grids: the float records as well
+    float* cells32;  // 16-/8-bit grids, full view: the float records as well
     int nx, ny, nz;
     const int* tile_stamp;
     const int* stamp_dev;
@@ -184,8 +184,12 @@ __device__ inline void store_cell(const float* p, size_t nx, size_t nxy, float* 
 template <typename T>
 __device__ inline void store_cell(const T* p, size_t nx, size_t nxy, T* cells, size_t idx)
 {
+    static_assert(sizeof(T) == 2 || sizeof(T) == 1, "16- or 8-bit storage");
     const T h[8] = {p[0], p[1], p[nx], p[nx + 1], p[nxy], p[nxy + 1], p[nxy + nx], p[nxy + nx + 1]};
-    reinterpret_cast<uint4*>(cells)[idx] = *reinterpret_cast<const uint4*>(h);
+    if (sizeof(T) == 2)
+        reinterpret_cast<uint4*>(cells)[idx] = *reinterpret_cast<const uint4*>(h);
+    else
+        reinterpret_cast<uint2*>(cells)[idx] = *reinterpret_cast<const uint2*>(h);
 }
 
 // The float record of a 16-bit grid: the stored values converted exactly and
@@ -248,6 +252,7 @@ pf_status enqueue_refresh(pf_volume* v, cudaStream_t s, int all)
     switch (v->desc.tsdf_dtype) {
     case PF_F16: cells_refresh_kernel<__half><<<grid, dim3(TX, TY), 0, s>>>(r); break;
     case PF_BF16: cells_refresh_kernel<__nv_bfloat16><<<grid, dim3(TX, TY), 0, s>>>(r); break;
+    case PF_FP8E4M3: cells_refresh_kernel<__nv_fp8_e4m3><<<grid, dim3(TX, TY), 0, s>>>(r); break;
     default: cells_refresh_kernel<float><<<grid, dim3(TX, TY), 0, s>>>(r); break;
     }
     pf::count_launch();
@@ -266,6 +271,9 @@ void dispatch_storage(const pf_volume* v, Args&&... args)
         break;
     case PF_BF16:
         if (u8) K<__nv_bfloat16, uint8_t>::run(args...); else K<__nv_bfloat16, float>::run(args...);
+        break;
+    case PF_FP8E4M3:
+        if (u8) K<__nv_fp8_e4m3, uint8_t>::run(args...); else K<__nv_fp8_e4m3, float>::run(args...);
         break;
     default:
         if (u8) K<float, uint8_t>::run(args...); else K<float, float>::run(args...);
@@ -300,10 +308,12 @@ pf_status check_desc(const pf_volume_desc* d)
     for (int a = 0; a < 3; ++a)
         if (!std::isfinite(d->origin[a])) return PF_ERR_INVALID_ARG;
     if (d->max_weight < 1 || d->max_weight > 65535) return PF_ERR_INVALID_ARG;
-    if (d->cell_view < -1 || d->cell_view > 1) return PF_ERR_INVALID_ARG;
+    if (d->cell_view < -1 || d->cell_view > 2) return PF_ERR_INVALID_ARG;
     if (d->weight_u8 != 0 && d->weight_u8 != 1) return PF_ERR_INVALID_ARG;
     if (d->weight_u8 && d->max_weight > 255) return PF_ERR_INVALID_ARG;
-    if (d->tsdf_dtype != PF_F32 && d->tsdf_dtype != PF_F16 && d->tsdf_dtype != PF_BF16) return PF_ERR_UNSUPPORTED;
+    if (d->tsdf_dtype != PF_F32 && d->tsdf_dtype != PF_F16 && d->tsdf_dtype != PF_BF16 &&
+        d->tsdf_dtype != PF_FP8E4M3)
+        return PF_ERR_UNSUPPORTED;
     return PF_OK;
 }
 
@@ -339,17 +349,31 @@ pf_status pf_create_volume(const pf_volume_desc* desc, void* stream, pf_volume**
     v->tiles[1] = (desc->ny + TY - 1) / TY;
     v->tiles[2] = (desc->nz + TZ - 1) / TZ;
     const size_t ts = pf_dtype_size(desc->tsdf_dtype), ws = desc->weight_u8 ? 1 : 4;
-    // a 16-bit grid keeps both its 16-bit records (lanes on points: two
-    // records per sector) and float records (lanes on particles: no
-    // conversions); a float grid has the float records only
+    // the full view of a 16-/8-bit grid keeps both its narrow records (lanes
+    // on points: two or four records per sector) and float records (lanes on
+    // particles: no conversions); the narrow view keeps the narrow records
+    // only; a float grid has the float records only
     const size_t bytes32 = desc->tsdf_dtype == PF_F32 ? 0 : v->n_nodes * 32;
     const size_t view_bytes = v->n_nodes * 8 * ts;
-    const bool view = desc->cell_view == 1 || (desc->cell_view == 0 && view_bytes + bytes32 <= (16ull << 30));
+    const size_t grid_bytes = v->n_nodes * (ts + ws);
     cudaError_t e = cudaGetDevice(&v->device);
+    int mode = desc->cell_view;
+    if (mode == 0) {
+        // auto, within half of the device memory free now: the full view
+        // when it fits (decoding narrow records on load slows the search
+        // once the particles converge), else the narrow one, else none
+        size_t free_b = 0, total_b = 0;
+        if (e == cudaSuccess) e = cudaMemGetInfo(&free_b, &total_b);
+        const size_t budget = free_b / 2;
+        mode = grid_bytes + view_bytes + bytes32 <= budget ? 1 : grid_bytes + view_bytes <= budget ? 2 : -1;
+    }
+    if (mode == 2 && !bytes32) mode = 1;
+    const bool view = mode >= 1;
+    const bool wide = mode == 1;
     if (e == cudaSuccess) e = cudaMalloc(&v->tsdf, v->n_nodes * ts);
     if (e == cudaSuccess) e = cudaMalloc(&v->weight, v->n_nodes * ws);
     if (e == cudaSuccess && view) e = cudaMalloc(&v->cells, view_bytes);
-    if (e == cudaSuccess && view && bytes32) e = cudaMalloc(&v->cells32, bytes32);
+    if (e == cudaSuccess && wide && bytes32) e = cudaMalloc(&v->cells32, bytes32);
     if (e == cudaSuccess && view)
         e = cudaMalloc(&v->tile_stamp, sizeof(int) * ((size_t)v->tiles[0] * v->tiles[1] * v->tiles[2] + 1));
     if (e == cudaSuccess && view)
@@ -413,34 +437,66 @@ pf_status pf_set_fitness_variant(pf_volume* v, int variant)
     return PF_OK;
 }
 
+pf_status pf_volume_info(const pf_volume* v, unsigned long long* storage_bytes, int* cell_view)
+{
+    if (!v) return PF_ERR_INVALID_ARG;
+    const size_t n = v->n_nodes, ts = pf_dtype_size(v->desc.tsdf_dtype);
+    const size_t n_tiles = (size_t)v->tiles[0] * v->tiles[1] * v->tiles[2];
+    size_t b = n * ts + n * (v->desc.weight_u8 ? 1 : 4);
+    if (v->cells) b += n * 8 * ts + sizeof(int) * (n_tiles + 1);
+    if (v->cells32) b += n * 32;
+    if (storage_bytes) *storage_bytes = b;
+    if (cell_view) *cell_view = !v->cells ? -1 : (v->cells32 || v->desc.tsdf_dtype == PF_F32) ? 1 : 2;
+    return PF_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+// Host-side conversion of one encoded value to and from the storage type.
+void store_host(pf_dtype dt, float e, unsigned char* dst)
+{
+    switch (dt) {
+    case PF_F16: { const __half h = pf_from_float<__half>(e); std::memcpy(dst, &h, 2); break; }
+    case PF_BF16: { const __nv_bfloat16 h = pf_from_float<__nv_bfloat16>(e); std::memcpy(dst, &h, 2); break; }
+    case PF_FP8E4M3: { const __nv_fp8_e4m3 h = pf_from_float<__nv_fp8_e4m3>(e); std::memcpy(dst, &h, 1); break; }
+    default: std::memcpy(dst, &e, 4); break;
+    }
+}
+
+float load_host(pf_dtype dt, const unsigned char* src)
+{
+    switch (dt) {
+    case PF_F16: { __half h; std::memcpy(&h, src, 2); return pf_to_float(h); }
+    case PF_BF16: { __nv_bfloat16 h; std::memcpy(&h, src, 2); return pf_to_float(h); }
+    case PF_FP8E4M3: { __nv_fp8_e4m3 h; std::memcpy(&h, src, 1); return pf_to_float(h); }
+    default: { float f; std::memcpy(&f, src, 4); return f; }
+    }
+}
+
+}  // namespace
+
+extern "C" {
+
 pf_status pf_volume_upload(pf_volume* v, const float* tsdf_host, const float* weight_host)
 {
     if (!v || !tsdf_host || !weight_host) return PF_ERR_INVALID_ARG;
     const size_t n = v->n_nodes;
     const pf_dtype dt = v->desc.tsdf_dtype;
-    std::vector<float> enc(dt == PF_F32 ? n : 0);
-    std::vector<uint16_t> enc16(dt == PF_F32 ? 0 : n);
+    const size_t ts = pf_dtype_size(dt);
+    std::vector<unsigned char> enc(n * ts);
     std::vector<uint8_t> w8(v->desc.weight_u8 ? n : 0);
     for (size_t i = 0; i < n; ++i) {
         const float w = weight_host[i];
         if (!(w >= 0.0f) || !std::isfinite(w) || w > (float)v->desc.max_weight) return PF_ERR_INVALID_ARG;
         if (w > 0.0f && !(std::fabs(tsdf_host[i]) <= 1.0f)) return PF_ERR_INVALID_ARG;
         if (v->desc.weight_u8 && w != std::floor(w)) return PF_ERR_INVALID_ARG;
-        const float e = pf_encode(tsdf_host[i], w);
-        if (dt == PF_F32) {
-            enc[i] = e;
-        } else if (dt == PF_F16) {
-            const __half h = pf_from_float<__half>(e);
-            std::memcpy(&enc16[i], &h, 2);
-        } else {
-            const __nv_bfloat16 h = pf_from_float<__nv_bfloat16>(e);
-            std::memcpy(&enc16[i], &h, 2);
-        }
+        store_host(dt, pf_encode(tsdf_host[i], w), enc.data() + i * ts);
         if (v->desc.weight_u8) w8[i] = (uint8_t)w;
     }
     PF_CUDA(cudaDeviceSynchronize());
-    if (dt == PF_F32) PF_CUDA(cudaMemcpy(v->tsdf, enc.data(), n * 4, cudaMemcpyHostToDevice));
-    else PF_CUDA(cudaMemcpy(v->tsdf, enc16.data(), n * 2, cudaMemcpyHostToDevice));
+    PF_CUDA(cudaMemcpy(v->tsdf, enc.data(), n * ts, cudaMemcpyHostToDevice));
     if (v->desc.weight_u8) PF_CUDA(cudaMemcpy(v->weight, w8.data(), n, cudaMemcpyHostToDevice));
     else PF_CUDA(cudaMemcpy(v->weight, weight_host, n * 4, cudaMemcpyHostToDevice));
     pf_status st = enqueue_refresh(v, 0, 1);
@@ -454,23 +510,14 @@ pf_status pf_volume_download(const pf_volume* v, float* tsdf_host, float* weight
     if (!v || !tsdf_host || !weight_host) return PF_ERR_INVALID_ARG;
     const size_t n = v->n_nodes;
     const pf_dtype dt = v->desc.tsdf_dtype;
+    const size_t ts = pf_dtype_size(dt);
     PF_CUDA(cudaDeviceSynchronize());
     if (dt == PF_F32) {
         PF_CUDA(cudaMemcpy(tsdf_host, v->tsdf, n * 4, cudaMemcpyDeviceToHost));
     } else {
-        std::vector<uint16_t> raw(n);
-        PF_CUDA(cudaMemcpy(raw.data(), v->tsdf, n * 2, cudaMemcpyDeviceToHost));
-        for (size_t i = 0; i < n; ++i) {
-            if (dt == PF_F16) {
-                __half h;
-                std::memcpy(&h, &raw[i], 2);
-                tsdf_host[i] = pf_to_float(h);
-            } else {
-                __nv_bfloat16 h;
-                std::memcpy(&h, &raw[i], 2);
-                tsdf_host[i] = pf_to_float(h);
-            }
-        }
+        std::vector<unsigned char> raw(n * ts);
+        PF_CUDA(cudaMemcpy(raw.data(), v->tsdf, n * ts, cudaMemcpyDeviceToHost));
+        for (size_t i = 0; i < n; ++i) tsdf_host[i] = load_host(dt, raw.data() + i * ts);
     }
     if (v->desc.weight_u8) {
         std::vector<uint8_t> w8(n);

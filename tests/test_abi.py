@@ -63,13 +63,16 @@ def test_host_side_validation_without_a_gpu(lib):
         pf.pf_volume_desc(8, 8, 8, 0.1, 0.3, (C.c_float * 3)(0, float("nan"), 0), pf.PF_F32, 0, 255),
         pf.pf_volume_desc(8, 8, 8, 0.1, 0.3, (C.c_float * 3)(0, 0, 0), pf.PF_F32, 0, 0),
         pf.pf_volume_desc(4096, 4096, 4096, 0.1, 0.3, (C.c_float * 3)(0, 0, 0), pf.PF_F32, 0, 255),
+        # cell view modes are -1, 0, 1, 2
+        pf.pf_volume_desc(8, 8, 8, 0.1, 0.3, (C.c_float * 3)(0, 0, 0), pf.PF_F32, 0, 255, 3),
+        pf.pf_volume_desc(8, 8, 8, 0.1, 0.3, (C.c_float * 3)(0, 0, 0), pf.PF_F16, 0, 255, -2),
     ]
     for d in bad:
         assert lib.pf_create_volume(C.byref(d), None, C.byref(out)) == pf.PF_ERR_INVALID_ARG
-    # storage types: 16-bit tsdf and uint8 weights exist, fp8 does not; a
-    # uint8 weight cannot count past 255
-    fp8 = pf.pf_volume_desc(8, 8, 8, 0.1, 0.3, (C.c_float * 3)(0, 0, 0), pf.PF_FP8E4M3, 0, 255)
-    assert lib.pf_create_volume(C.byref(fp8), None, C.byref(out)) == pf.PF_ERR_UNSUPPORTED
+    # storage types: f32, f16, bf16 and scaled e4m3 tsdf and uint8 weights
+    # exist, other codes do not; a uint8 weight cannot count past 255
+    bad_type = pf.pf_volume_desc(8, 8, 8, 0.1, 0.3, (C.c_float * 3)(0, 0, 0), 7, 0, 255)
+    assert lib.pf_create_volume(C.byref(bad_type), None, C.byref(out)) == pf.PF_ERR_UNSUPPORTED
     for dt, u8, mw in ((pf.PF_F16, 1, 256), (pf.PF_BF16, 2, 255), (pf.PF_F32, -1, 10)):
         d = pf.pf_volume_desc(8, 8, 8, 0.1, 0.3, (C.c_float * 3)(0, 0, 0), dt, u8, mw)
         assert lib.pf_create_volume(C.byref(d), None, C.byref(out)) == pf.PF_ERR_INVALID_ARG
@@ -83,6 +86,7 @@ def test_host_side_validation_without_a_gpu(lib):
     assert lib.pf_align_loss(None, None, None, 0, 1, None, None, None, None, None, None, None,
                              None) == pf.PF_ERR_INVALID_ARG
     assert lib.pf_polish(None, None, None, 0, None, 10, None, None, None) == pf.PF_ERR_INVALID_ARG
+    assert lib.pf_volume_info(None, None, None) == pf.PF_ERR_INVALID_ARG
     bout = C.c_void_p()
     assert lib.pf_batch_create(0, None, None, None, 1, C.byref(bout)) == pf.PF_ERR_INVALID_ARG
     assert lib.pf_batch_create(1, (C.c_void_p * 1)(None), C.byref(intr), None, 1,

@@ -1,5 +1,6 @@
-"""Reduced-precision storage: half / bfloat16 TSDF (and cell view), uint8
-fusion weights.  Every operation stays float; only stored values narrow.
+"""Reduced-precision storage: half / bfloat16 / scaled e4m3 TSDF (and cell
+view), uint8 fusion weights.  Every operation stays float; only stored
+values narrow.
 
 Two questions, two kinds of test.
   1. Is the arithmetic unchanged?  A 16-bit volume holds a rounded grid.  The
@@ -10,8 +11,8 @@ Two questions, two kinds of test.
      average (Sec. III-A) re-rounds the stored value, and the average only
      damps earlier errors (factor w / (w + 1)), so after n updates a node is
      off the FP64 result by at most n half-units-in-the-last-place of the
-     format just below 1 (2^-12 for half, 2^-9 for bfloat16) plus the float
-     tolerance.  Weights are integers below 256 and stay exact in uint8.
+     format just below 1 (2^-12 for half, 2^-9 for bfloat16, 2^-5 for e4m3
+     holding 256 x the value) plus the float tolerance.  Weights are integers below 256 and stay exact in uint8.
 The measured deviations are printed (run with -s to see them).
 """
 import numpy as np
@@ -26,8 +27,19 @@ from gpu_helpers import (abi, compare_fitness, load_pf, perturbed_poses, pose_ro
 
 pytestmark = pytest.mark.gpu
 
-# half-ulp just below 1.0 of each storage format
-HALF_ULP = {"f16": 2.0 ** -12, "bf16": 2.0 ** -9}
+# half-ulp just below 1.0 of each storage format (e4m3 holds 256 x the
+# value: in [128, 256) its step is 16, i.e. 1/16 of the value's unit)
+HALF_ULP = {"f16": 2.0 ** -12, "bf16": 2.0 ** -9, "fp8": 2.0 ** -5}
+
+
+def _e4m3_values():
+    """All non-negative finite e4m3 values by code (bias 7, 3 mantissa bits,
+    subnormals at exponent 0, the all-ones code is NaN)."""
+    out = []
+    for code in range(0x7f):
+        e, m = code >> 3, code & 7
+        out.append(m / 8.0 * 2.0 ** -6 if e == 0 else (1 + m / 8.0) * 2.0 ** (e - 7))
+    return np.array(out)
 
 
 @pytest.fixture(scope="module")
@@ -37,7 +49,7 @@ def pf():
 
 
 def dtype_code(pf, name):
-    return {"f32": pf.PF_F32, "f16": pf.PF_F16, "bf16": pf.PF_BF16}[name]
+    return {"f32": pf.PF_F32, "f16": pf.PF_F16, "bf16": pf.PF_BF16, "fp8": pf.PF_FP8E4M3}[name]
 
 
 def round_storage(x, name):
@@ -50,6 +62,16 @@ def round_storage(x, name):
         b = x.view(np.uint32).astype(np.uint64)
         r = (b + 0x7FFF + ((b >> 16) & 1)) & 0xFFFF0000
         return r.astype(np.uint32).view(np.float32)
+    if name == "fp8":
+        # 256 x the value to the nearest e4m3 value (ties to the even code)
+        vals = _e4m3_values()
+        a = np.abs(x.astype(np.float64)) * 256.0
+        hi = np.clip(np.searchsorted(vals, a), 1, len(vals) - 1)
+        lo = hi - 1
+        dlo, dhi = a - vals[lo], vals[hi] - a
+        pick = np.where(dlo < dhi, lo, np.where(dhi < dlo, hi, np.where(lo % 2 == 0, lo, hi)))
+        pick = np.where(a >= vals[-1], len(vals) - 1, pick)
+        return (np.sign(x) * vals[pick] / 256.0).astype(np.float32)
     return x
 
 
@@ -72,7 +94,7 @@ def _room_inputs(seed=0, holes=0.03):
 # storage round trip
 # ---------------------------------------------------------------------------
 
-@pytest.mark.parametrize("name,u8", [("f16", 0), ("bf16", 0), ("f16", 1), ("f32", 1)])
+@pytest.mark.parametrize("name,u8", [("f16", 0), ("bf16", 0), ("f16", 1), ("f32", 1), ("fp8", 1)])
 def test_upload_download_rounds_to_storage(pf, name, u8):
     scene, fr, tsdf, weight = _room_inputs()
     weight = np.minimum(weight, 200).astype(np.float32)
@@ -95,11 +117,15 @@ def test_upload_download_rounds_to_storage(pf, name, u8):
 # arithmetic parity on the stored grid
 # ---------------------------------------------------------------------------
 
-@pytest.mark.parametrize("name", ["f16", "bf16"])
-@pytest.mark.parametrize("K,N,spread", [(1024, None, 8.0), (1000, 12345, 0.05), (37, 777, 1.0)])
-def test_fitness_parity_on_stored_grid(pf, name, K, N, spread):
+@pytest.mark.parametrize("name", ["f16", "bf16", "fp8"])
+@pytest.mark.parametrize("K,N,spread,view", [(1024, None, 8.0, 1), (1000, 12345, 0.05, 1), (37, 777, 1.0, 1),
+                                             (1024, None, 8.0, 2), (1000, 12345, 0.05, 2)])
+def test_fitness_parity_on_stored_grid(pf, name, K, N, spread, view):
+    """view 1: the full cell view (lanes on particles read float records);
+    2: the narrow view (they convert the 16-/8-bit records on load)."""
     scene, fr, tsdf, weight = _room_inputs()
-    vol = pf.Volume.from_grid(synth.ROOM64_GRID, tsdf_dtype=dtype_code(pf, name))
+    vol = pf.Volume.from_grid(synth.ROOM64_GRID, tsdf_dtype=dtype_code(pf, name), cell_view=view)
+    assert vol.info()["cell_view"] == view
     vol.upload(tsdf, weight)
     ts, ws = vol.download()
     ovol = oracle.Volume(abi(synth.ROOM64_GRID), ts, ws)
@@ -116,7 +142,9 @@ def test_fitness_parity_on_stored_grid(pf, name, K, N, spread):
             E, C = vol.fitness(to_dev(pts), to_dev(poses))
             results[layout, mapping] = (E.cpu().numpy(), C.cpu().numpy())
             compare_fitness(*results[layout, mapping], orc)
-        if mapping > 0:
+        # (e4m3 cell records are read in a scaled form, so their roundings
+        # differ from the node layout's; 16-bit records are bit-identical)
+        if mapping > 0 and name != "fp8":
             assert np.array_equal(results[2, mapping][0], results[3, mapping][0])
     # the plain layout reads float arrays and is refused for 16-bit storage
     with pytest.raises(pf.ProfusionError):
@@ -124,12 +152,14 @@ def test_fitness_parity_on_stored_grid(pf, name, K, N, spread):
 
 
 @pytest.mark.parametrize("name", ["f16", "bf16"])
-def test_cell_view_follows_fusion_16bit(pf, name):
-    """After fusion into a 16-bit grid the cell view (raw corners) gives the
-    same fitness as the node layout, bit for bit."""
+@pytest.mark.parametrize("view,mapping", [(1, 1), (2, 1), (1, 2), (2, 2)])
+def test_cell_view_follows_fusion_16bit(pf, name, view, mapping):
+    """After fusion into a 16-bit grid the cell view (raw corners, and float
+    records in the full view) gives the same fitness as the node layout, bit
+    for bit, with lanes on points (mapping 1) and on particles (2)."""
     grid, intr = synth.ROOM64_GRID, synth.ROOM64_INTR
     scene = synth.room_scene(0)
-    vol = pf.Volume.from_grid(grid, tsdf_dtype=dtype_code(pf, name), weight_u8=1)
+    vol = pf.Volume.from_grid(grid, tsdf_dtype=dtype_code(pf, name), weight_u8=1, cell_view=view)
     for j in (0, 1, 2):
         P = synth.room_view(scene, j)
         vol.integrate(to_dev(synth.add_depth_noise(synth.render_depth(scene, intr, P), 50 + j, 0.002)), intr, P)
@@ -138,14 +168,38 @@ def test_cell_view_follows_fusion_16bit(pf, name):
     poses = to_dev(perturbed_poses(P, 512, 4.0, 4.0, seed=3))
     out = []
     for layout in (2, 3):
-        vol.set_fitness_variant(layout + 4)
+        vol.set_fitness_variant(layout + 4 * mapping)
         E, C = vol.fitness(pts, poses)
         out.append((E.cpu().numpy(), C.cpu().numpy()))
     assert np.count_nonzero(out[0][1]) > 100
     assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
 
 
-@pytest.mark.parametrize("name", ["f16", "bf16"])
+def test_volume_info_reports_storage_and_view(pf):
+    grid = synth.ROOM64_GRID
+    n = grid.n_nodes
+    info = {}
+    for name, ts in (("f32", 4), ("f16", 2), ("bf16", 2), ("fp8", 1)):
+        for view in (-1, 0, 1, 2):
+            vol = pf.Volume.from_grid(grid, tsdf_dtype=dtype_code(pf, name), weight_u8=1, cell_view=view)
+            info[name, view] = vol.info()
+            vol.close()
+        assert info[name, -1] == {"storage_bytes": n * (ts + 1), "cell_view": -1}
+        # a small grid takes the full view on its own
+        assert info[name, 0] == info[name, 1] and info[name, 1]["cell_view"] == 1
+        full, narrow = info[name, 1]["storage_bytes"], info[name, 2]["storage_bytes"]
+        if name == "f32":
+            assert info[name, 2] == info[name, 1]
+        else:
+            assert info[name, 2]["cell_view"] == 2 and full - narrow == 32 * n
+        # records of 8 values, plus a few bytes of fusion stamps
+        assert 0 <= narrow - n * (ts + 1) - 8 * ts * n < 65536
+    print("\nprecision: storage bytes per node (u8 weights; none / narrow / full view): " + ", ".join(
+        f"{nm} {info[nm, -1]['storage_bytes'] / n:.0f}/{info[nm, 2]['storage_bytes'] / n:.0f}/"
+        f"{info[nm, 1]['storage_bytes'] / n:.0f}" for nm in ("f32", "f16", "bf16", "fp8")))
+
+
+@pytest.mark.parametrize("name", ["f16", "bf16", "fp8"])
 def test_track_parity_on_stored_grid(pf, name):
     torch = torch_cuda()
     K, iters = 1024, 10
@@ -188,7 +242,7 @@ FUSION = {
 
 
 @pytest.mark.parametrize("case", sorted(FUSION))
-@pytest.mark.parametrize("name,u8", [("f16", 0), ("bf16", 0), ("f16", 1), ("bf16", 1), ("f32", 1)])
+@pytest.mark.parametrize("name,u8", [("f16", 0), ("bf16", 0), ("f16", 1), ("bf16", 1), ("f32", 1), ("fp8", 1)])
 def test_fusion_error_bound(pf, case, name, u8):
     grid, intr = FUSION[case]
     scene = synth.room_scene(0)
