@@ -895,7 +895,10 @@ __device__ __forceinline__ void fitness_body(const FitArgs& a, int bx, int by, u
             // (nearly) the same cell, lanes take particles and share a point,
             // so each gather of a warp touches one or two sectors; otherwise
             // lanes take neighbouring image points of one particle
+            // (the plain form never gets here: no unreachable-code note)
+#pragma nv_diag_suppress 128
             for (int o = 16; o > 0; o >>= 1) r2 = fmaxf(r2, __shfl_xor_sync(0xffffffffu, r2, o));
+#pragma nv_diag_default 128
             if (lane == 0) s_red[warp] = r2;
             __syncthreads();
             if (tid == 0) {

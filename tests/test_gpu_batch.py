@@ -34,14 +34,15 @@ def pf():
     return load_pf()
 
 
-def _setup(pf, seed=0):
+def _setup(pf, seed=0, dtype=None, views=(0, 0, 0)):
     """Volumes fused from three noise-free views each, the frame to track
     (noisy) and its initial pose per sequence."""
     torch = torch_cuda()
     scene = synth.room_scene(seed)
     vols, frames = [], []
-    for g, intr, view in SEQS:
-        v = pf.Volume.from_grid(g)
+    for (g, intr, view), cv in zip(SEQS, views):
+        v = pf.Volume.from_grid(g, tsdf_dtype=pf.PF_F32 if dtype is None else dtype, cell_view=cv,
+                                weight_u8=int(dtype is not None))
         for j in range(3):
             P = synth.room_view(scene, (view + 1 + j) % 8)
             v.integrate(to_dev(synth.render_depth(scene, intr, P)), intr, P)
@@ -64,9 +65,23 @@ def _load_inputs(batch, frames):
         batch.rel[i].copy_(to_dev(np.eye(4)))
 
 
-def test_batch_step_matches_the_oracle_per_sequence(pf):
+STORAGE = {"f32": ("PF_F32", (0, 0, 0)), "bf16": ("PF_BF16", (0, 0, 0)), "fp8": ("PF_FP8E4M3", (0, 0, 0)),
+           "f16-narrow": ("PF_F16", (2, 2, 2)), "fp8-mixed-views": ("PF_FP8E4M3", (1, 2, 1))}
+
+
+@pytest.mark.parametrize("storage", sorted(STORAGE))
+def test_batch_step_matches_the_oracle_per_sequence(pf, storage):
+    """Per storage type (uint8 weights for the narrow ones) and cell view
+    (full, narrow, or mixed within the batch): the oracle runs on each
+    volume's downloaded grid, i.e. the stored values.  Decisions are compared
+    while the oracle's margins stay clear (at least one iteration per
+    sequence, four over the batch); the final pose always."""
     torch = torch_cuda()
-    vols, frames, templ, params = _setup(pf)
+    code, views = STORAGE[storage]
+    dtype = None if storage == "f32" else getattr(pf, code)
+    vols, frames, templ, params = _setup(pf, dtype=dtype, views=views)
+    for v, cv in zip(vols, views):
+        assert v.info()["cell_view"] == (cv or 1)
     grids = [v.download() for v in vols]  # the state each search runs against
     batch = pf.Batch(vols, [s[1] for s in SEQS], params, use_graph=True)
     _load_inputs(batch, frames)
@@ -74,6 +89,7 @@ def test_batch_step_matches_the_oracle_per_sequence(pf):
     torch.cuda.synchronize()
     oparams = oracle.TrackParams(n_iters=ITERS, k_sched=(K, K, K), decim_sched=(1, 1, 1), update_mode=0,
                                  compose_mode=1)
+    total_strict = 0
     for i, ((g, intr, view), (depth, gt, init)) in enumerate(zip(SEQS, frames)):
         st = batch.stats_dict(i)
         pose = batch.pose[i].cpu().numpy()
@@ -88,8 +104,10 @@ def test_batch_step_matches_the_oracle_per_sequence(pf):
                 break
             strict += 1
             assert st["best"][it] == os_["best"][it] and st["n_adv"][it] == os_["n_adv"][it], (i, it)
-        assert strict >= 2, i
+        assert strict >= 1, i
+        total_strict += strict
         assert pose_trans_err(pose, ores.pose) <= 1e-4 and pose_rot_err(pose, ores.pose) <= 1e-4, i
+    assert total_strict >= 4
     batch.close()
 
 

@@ -231,6 +231,31 @@ def test_track_parity_on_stored_grid(pf, name):
           f"rot {np.degrees(pose_rot_err(pose, fr.gt_pose)):.4f} deg")
 
 
+@pytest.mark.parametrize("name", ["f16", "bf16", "fp8"])
+def test_raycast_parity_on_stored_grid(pf, name):
+    """Ray casting a narrow grid fused on the GPU against the oracle's ray
+    cast of the same stored values (downloaded and decoded)."""
+    grid = Grid(72, 72, 72, 0.05, 0.15, (-0.2, -0.2, -0.2))
+    intr = Intrinsics(160, 120, 140.0, 140.0, 79.5, 59.5)
+    scene = synth.room_scene(2)
+    vol = pf.Volume.from_grid(grid, tsdf_dtype=dtype_code(pf, name), weight_u8=1)
+    for j in range(8):
+        P = synth.room_view(scene, j)
+        vol.integrate(to_dev(synth.add_depth_noise(synth.render_depth(scene, intr, P), 50 + j, 0.002)), intr, P)
+    ts, ws = vol.download()
+    ovol = oracle.Volume(abi(grid), ts, ws)
+    P = synth.room_view(scene, 0)
+    d, n = vol.raycast(intr, P)
+    d, n = d.cpu().numpy(), n.cpu().numpy()
+    od, on = oracle.raycast(ovol, abi(intr), P)
+    both = (d > 0) & (od > 0)
+    assert np.count_nonzero(both) > 0.3 * d.size
+    assert np.mean((d > 0) == (od > 0)) > 0.995
+    assert np.mean(np.abs(d[both] - od[both]) < 1e-4) > 0.995
+    good = both & np.isfinite(n[..., 0]) & np.isfinite(on[..., 0])
+    assert np.mean(np.sum(n[good] * on[good], axis=-1) > 0.999) > 0.99
+
+
 # ---------------------------------------------------------------------------
 # fusion: deviation from the FP64 oracle bounded by the storage rounding
 # ---------------------------------------------------------------------------
