@@ -8,11 +8,13 @@ Two questions, two kinds of test.
      same rounded grid (downloaded and decoded) with the float-storage
      tolerances of the parity tests.
   2. How far does the rounding move fusion?  Each update of the running
-     average (Sec. III-A) re-rounds the stored value, and the average only
-     damps earlier errors (factor w / (w + 1)), so after n updates a node is
-     off the FP64 result by at most n half-units-in-the-last-place of the
-     format just below 1 (2^-12 for half, 2^-9 for bfloat16, 2^-5 for e4m3
-     holding 256 x the value) plus the float tolerance.  Weights are integers below 256 and stay exact in uint8.
+     average (Sec. III, fusion as in KinectFusion) re-rounds the stored
+     value, and the average only damps earlier errors (factor w / (w + 1)),
+     so after n updates a node is off the FP64 result by at most n
+     half-units-in-the-last-place of the format just below 1 (2^-12 for
+     half, 2^-9 for bfloat16, 2^-5 for e4m3 holding 256 x the value) plus
+     the float tolerance.  Weights are integers below 256 and stay exact in
+     uint8.
 The measured deviations are printed (run with -s to see them).
 """
 import numpy as np
