@@ -775,10 +775,16 @@ long or_integrate(double* tsdf, double* weight, const or_grid* g, const float* d
                 double yc = R[1] * d[0] + R[5] * d[1] + R[9] * d[2];
                 double zc = R[2] * d[0] + R[6] * d[1] + R[10] * d[2];
                 if (mask) mask[idx] = 0;
+                /* a node within eps_m of the camera plane may fall on either
+                 * side of z = 0 */
+                if (mask && fabs(zc) < eps_m) {
+                    mask[idx] = 1;
+                    ++amb;
+                }
                 if (!(zc > 0.0)) continue;
                 double u = in->fx * xc / zc + in->cx;
                 double v = in->fy * yc / zc + in->cy;
-                if (mask) {
+                if (mask && !mask[idx]) {
                     double fu = u + 0.5 - floor(u + 0.5), fv = v + 0.5 - floor(v + 0.5);
                     int near_u = fu < eps_px || fu > 1.0 - eps_px;
                     int near_v = fv < eps_px || fv > 1.0 - eps_px;
