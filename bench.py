@@ -825,6 +825,9 @@ def run_batch(args):
         for f in range(1, W + 1):
             load(f)
             batch.step()
+            if f == 1:
+                p1 = np.stack([batch.pose[i].cpu().numpy().reshape(16) for i in range(BATCH_SEQS)])
+                out["pose_diff_1_m"] = float(np.max(np.abs(p1[:, 3::4][:, :3] - pose_seq[:, 1, 3::4][:, :3])))
         times = []
         for f in range(W + 1, W + S + 1):
             load(f)  # input copies stay outside the timed region
@@ -845,6 +848,7 @@ def run_batch(args):
         "speedup_graph_vs_sequential": ms_seq / out["graph"],
         "speedup_graph_vs_plain_f32_sequential": ms_plain / out["graph"],
         "points_per_block": out.get("points_per_block"),
+        "max_position_difference_batch_vs_sequential_after_first_step_m": out.get("pose_diff_1_m"),
         "max_final_position_difference_batch_vs_sequential_m": out["pose_diff_m"],
     }))
     for v in vols:

@@ -346,6 +346,54 @@ def test_track_decimated_schedule(pf):
     assert pose_trans_err(pose, ores.pose) <= 1e-4 and pose_rot_err(pose, ores.pose) <= 1e-4
 
 
+def test_track_paper_schedule_with_10240_particles(pf):
+    """The paper's schedule at full scale in particles: 1024 / 3072 / 10240
+    particles with strides 8 / 16 / 32 (Sec. IV-A), mean update."""
+    torch = torch_cuda()
+    scene, fr, tsdf, weight = _room_inputs(2, holes=0.0)
+    vol = pf.Volume.from_grid(synth.ROOM64_GRID)
+    vol.upload(tsdf, weight)
+    ovol = oracle.Volume(abi(synth.ROOM64_GRID), tsdf, weight)
+    templ = synth.templates(10240, 2)
+    ks, ds = (1024, 3072, 10240), (8, 16, 32)
+    params = pf.track_params(torch.from_numpy(templ).cuda(), n_iters=6, k_sched=ks, decim_sched=ds,
+                             update_mode=0, compose_mode=1)
+    status, pose, st = vol.track_frame(to_dev(fr.depth), synth.ROOM64_INTR, params, fr.init_pose)
+    ores = oracle.track(ovol, fr.depth, abi(synth.ROOM64_INTR), templ, fr.init_pose,
+                        oracle.TrackParams(n_iters=6, k_sched=ks, decim_sched=ds, update_mode=0, compose_mode=1))
+    assert status == pf.PF_OK and not ores.lost
+    os_ = ores.stats
+    assert list(st["k_used"]) == list(os_["k_used"]) == [1024, 3072, 10240, 1024, 3072, 10240]
+    assert list(st["n_eval"]) == list(os_["n_eval"])
+    for i in range(6):
+        if not (os_["best_gap"][i] > 3e-5 and os_["adv_margin"][i] > 3e-5):
+            break
+        assert st["best"][i] == os_["best"][i] and st["n_adv"][i] == os_["n_adv"][i], i
+    assert pose_trans_err(pose, ores.pose) <= 1e-4 and pose_rot_err(pose, ores.pose) <= 1e-4
+
+
+def test_track_exact_ties_on_a_constant_field(pf):
+    """A constant field c (exact in binary): every particle ties exactly, so
+    the best index is 0 (lowest on ties), the advantage set is empty, the
+    pose stays, and s follows s0 (beta + (1 - beta) c)^i in both modes."""
+    torch = torch_cuda()
+    g = Grid(30, 30, 30, 0.1, 0.3, (-1.5, -1.5, 0.0))
+    c = 0.375
+    vol = pf.Volume.from_grid(g)
+    vol.upload(np.full(g.n_nodes, c, dtype=np.float32), np.ones(g.n_nodes, dtype=np.float32))
+    intr = Intrinsics(6, 5, 5.0, 5.0, 2.5, 2.0)
+    depth = np.full((5, 6), 1.5, dtype=np.float32)
+    templ = torch.from_numpy(synth.templates(64, 1)).cuda()
+    for mode in (0, 1):
+        params = pf.track_params(templ, n_iters=8, k_sched=(64, 64, 64), decim_sched=(1, 1, 1), update_mode=mode)
+        status, pose, st = vol.track_frame(to_dev(depth), intr, params, np.eye(4))
+        assert status == pf.PF_OK
+        assert np.all(st["n_adv"] == 0) and np.all(st["best"] == 0)
+        assert np.array_equal(pose, np.eye(4))
+        assert np.all(st["E0"] == np.float32(c))
+        np.testing.assert_allclose(st["s"][:, 0], 10.0 * (0.1 + 0.9 * c) ** np.arange(8), rtol=1e-12)
+
+
 # ---------------------------------------------------------------------------
 # raycast
 # ---------------------------------------------------------------------------
