@@ -44,6 +44,9 @@
 extern "C" {
 #endif
 
+/* Status of every call.  PF_ERR_TIMEOUT is reserved: no call waits on the
+ * device (kernels never spin on flags or on one another; ordering comes from
+ * stream order). */
 typedef enum {
     PF_OK = 0,
     PF_ERR_INVALID_ARG = 1,
