@@ -111,6 +111,67 @@ def test_batch_step_matches_the_oracle_per_sequence(pf, storage):
     batch.close()
 
 
+def test_many_small_sequences_match_the_oracle(pf):
+    """64 sequences of different grids (20^3 .. 27^3 nodes over the room),
+    cameras (40x30 .. 71x53) and particle counts (64 .. 256): every CTA finds
+    its problem among 64 in the batched launches; each sequence's search
+    matches the oracle on its own fused grid."""
+    torch = torch_cuda()
+    scene = synth.room_scene(3)
+    n = 64
+    vols, gdefs, cams, frames, params, kk = [], [], [], [], [], []
+    templ_np = synth.templates(256, 3)
+    templ = torch.from_numpy(templ_np).cuda()
+    for i in range(n):
+        m = 20 + i % 8
+        g = Grid(m, m, m, 3.6 / (m - 1), 3.0 * 3.6 / (m - 1), (-0.2, -0.2, -0.2))
+        w, h = 40 + (i * 7) % 32, 30 + (i * 5) % 24
+        cam = Intrinsics(w, h, 0.9 * w, 0.9 * w, (w - 1) / 2, (h - 1) / 2, 0.1, 8.0)
+        v = pf.Volume.from_grid(g)
+        for j in range(2):
+            P = synth.room_view(scene, (i + 1 + j) % 8)
+            v.integrate(to_dev(synth.render_depth(scene, cam, P)), cam, P)
+        gt = synth.room_view(scene, i % 8)
+        depth = synth.add_depth_noise(synth.render_depth(scene, cam, gt), 500 + i, 0.001)
+        init = gt @ synth.perturbation(600 + i, 0, 3.0, 3.0)
+        K_i = (64, 128, 192, 256)[i % 4]
+        vols.append(v)
+        gdefs.append(g)
+        cams.append(cam)
+        frames.append((depth, gt, init))
+        kk.append(K_i)
+        params.append(pf.track_params(templ, n_iters=4, k_sched=(K_i,) * 3, decim_sched=(1, 1, 1), update_mode=0,
+                                      compose_mode=1))
+    torch.cuda.synchronize()
+    grids = [v.download() for v in vols]
+    batch = pf.Batch(vols, cams, params, use_graph=False)
+    _load_inputs(batch, frames)
+    batch.step()
+    torch.cuda.synchronize()
+    total_strict = 0
+    for i in range(n):
+        depth, gt, init = frames[i]
+        st = batch.stats_dict(i)
+        pose = batch.pose[i].cpu().numpy()
+        ovol = oracle.Volume(abi(gdefs[i]), *grids[i])
+        ores = oracle.track(ovol, depth, abi(cams[i]), templ_np, init,
+                            oracle.TrackParams(n_iters=4, k_sched=(kk[i],) * 3, decim_sched=(1, 1, 1), update_mode=0,
+                                               compose_mode=1))
+        assert st["status"] == (pf.PF_ERR_TRACK_LOST if ores.lost else pf.PF_OK), i
+        if ores.lost:
+            continue
+        os_ = ores.stats
+        assert st["n_points"] == os_["n_points"], i
+        for it in range(4):
+            if not (os_["best_gap"][it] > 3e-5 and os_["adv_margin"][it] > 3e-5):
+                break
+            total_strict += 1
+            assert st["best"][it] == os_["best"][it] and st["n_adv"][it] == os_["n_adv"][it], (i, it)
+        assert pose_trans_err(pose, ores.pose) <= 1e-4 and pose_rot_err(pose, ores.pose) <= 1e-4, i
+    assert total_strict >= n
+    batch.close()
+
+
 def test_graph_replay_equals_direct_launches(pf):
     torch = torch_cuda()
     results = []

@@ -246,6 +246,26 @@ def test_fitness_edge_cases(pf):
     assert torch.all(C == 0)
 
 
+def test_fitness_at_the_maximum_pose_count(pf):
+    """k = 65536, the largest pose count pf_fitness takes, over every point
+    of a room-64 frame, against the oracle; k = 65537 is refused before
+    anything runs."""
+    torch = torch_cuda()
+    scene, fr, tsdf, weight = _room_inputs()
+    vol = pf.Volume.from_grid(synth.ROOM64_GRID)
+    vol.upload(tsdf, weight)
+    ovol = oracle.Volume(abi(synth.ROOM64_GRID), tsdf, weight)
+    pts = synth.render_points(scene, synth.ROOM64_INTR, fr.gt_pose)
+    poses = perturbed_poses(fr.gt_pose, 65536, 5.0, 5.0, seed=77)
+    E, C = vol.fitness(to_dev(pts), to_dev(poses))
+    orc = oracle.fitness(ovol, pts, poses, ambiguity=True, cap=64)
+    assert np.all(orc.amb <= 64)
+    compare_fitness(E.cpu().numpy(), C.cpu().numpy(), orc)
+    too_many = torch.zeros((65537, 12), dtype=torch.float32, device="cuda")
+    with pytest.raises(pf.ProfusionError):
+        vol.fitness(to_dev(pts), too_many)
+
+
 def test_fitness_is_deterministic(pf):
     scene, fr, tsdf, weight = _room_inputs()
     vol = pf.Volume.from_grid(synth.ROOM64_GRID)
