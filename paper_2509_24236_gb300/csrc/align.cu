@@ -35,6 +35,7 @@
 //     candidate [Exp(d_omega) | d_v] T.  No host round trip: a polish is a
 //     fixed launch sequence.
 #include <algorithm>
+#include <climits>
 #include <mutex>
 #include <unordered_map>
 
@@ -46,7 +47,9 @@ constexpr int AL_THREADS = 256;
 constexpr int AL_TILES = 296;          // most point tiles per frame (2 per SM)
 constexpr int AL_BLOCKS = 2432;        // target blocks per launch (2 waves of 8 per SM)
 constexpr int RED_THREADS = 256;       // tile reductions
-constexpr double kFix = 1099511627776.0;  // 2^40, fixed-point scale of dL/dV
+// dL/dV accumulates in int64 units of 2^-40 (fix40 / fixed40_to_float)
+constexpr float kRound = 12582912.0f;  // 1.5 * 2^23: adding it rounds |v| < 2^22 to an integer
+constexpr int kRoundBits = 0x4B400000;  // its bit pattern
 constexpr int GN_VALS = 29;            // 21 (upper H) + 6 (b) + loss + count
 
 struct AlignScratch {
@@ -55,6 +58,9 @@ struct AlignScratch {
     long long* acc = nullptr;     // n_nodes fixed-point dL/dV
     double* gn_part = nullptr;    // AL_TILES x GN_VALS
     double* gn_state = nullptr;   // see GnState
+    void* frame_pose = nullptr;   // frames x FramePose (the poses prepared once per frame)
+    int frame_cap = 0;            // frames
+    void* gn_pose = nullptr;      // one PoseF: the polish's candidate, prepared once per step
 };
 
 std::mutex g_mu;
@@ -168,6 +174,28 @@ __device__ inline void make_posef(const double T[12], const GridInfo& g, PoseF& 
     }
 }
 
+// One frame of pf_align_loss, prepared once per frame (FP64 work that every
+// block of the frame would otherwise repeat): the perturbed pose for
+// sampling, the translation part v of the perturbation (q - v enters the
+// rotation gradient) and the weight 2 W of the node gradient.
+struct FramePose {
+    PoseF P;
+    float V[3];
+    float w2;
+};
+
+// Copy a record of 4-byte words from global to shared memory with the
+// whole block (call from every thread; a barrier follows).
+template <typename T>
+__device__ inline void block_copy_words(const T* src, T* dst)
+{
+    static_assert(sizeof(T) % 4 == 0, "4-byte words");
+    const int* s = reinterpret_cast<const int*>(src);
+    int* d = reinterpret_cast<int*>(dst);
+    for (int i = threadIdx.x; i < (int)(sizeof(T) / 4); i += blockDim.x) d[i] = s[i];
+    __syncthreads();
+}
+
 // y = (hi + lo) . x as an integer part and a float fraction, to ~1e-12 of
 // |y|: the products are split exactly (p = hi*x rounded, fma(hi, x, -p) its
 // error), the three-term sum carries its rounding errors (two-sum), and the
@@ -185,8 +213,11 @@ __device__ inline bool row_split(const float* hi, const float* lo, float x, floa
     err = __fadd_rn(err, __fadd_rn(__fsub_rn(s1, __fsub_rn(s2, bb)), __fsub_rn(p2, bb)));
     err = fmaf(lo[0], x, fmaf(lo[1], y, fmaf(lo[2], z, err)));
     if (!(fabsf(s2) < 4194304.0f)) return false;
-    const float r = rintf(s2);
-    yi = (int)r;
+    // nearest integer (ties to even) by adding 1.5 * 2^23, whose unit in the
+    // last place is 1; its bits give the integer without a conversion
+    const float m = __fadd_rn(s2, kRound);
+    const float r = __fsub_rn(m, kRound);
+    yi = __float_as_int(m) - kRoundBits;
     yf = __fadd_rn(__fsub_rn(s2, r), err);
     return true;
 }
@@ -208,8 +239,10 @@ __device__ inline bool sample_f(const TS* tsdf, const GridInfo& g, const PoseF& 
         float yf;
         if (!row_split(P.Ahi + 3 * r, P.Alo + 3 * r, x, y, z, yi, yf)) return false;
         const float u = __fadd_rn(yf, P.b[r]);
-        const float fl = floorf(u);
-        ci[r] = (long long)P.o[r] + yi + (long long)fl;
+        // floor(u) the same way with round-down (|u| is a few units)
+        const float m = __fadd_rd(u, kRound);
+        const float fl = __fsub_rn(m, kRound);
+        ci[r] = (long long)P.o[r] + yi + (long long)(__float_as_int(m) - kRoundBits);
         f[r] = __fsub_rn(u, fl);
         if (ci[r] < 0 || ci[r] > n[r] - 2) return false;
     }
@@ -243,23 +276,110 @@ __device__ inline void transform_f(const PoseF& P, float x, float y, float z, fl
     for (int r = 0; r < 3; ++r) q[r] = fmaf(P.R[3 * r], x, fmaf(P.R[3 * r + 1], y, fmaf(P.R[3 * r + 2], z, P.t[r])));
 }
 
-// Fixed-order block sum of NV doubles per thread; thread 0 gets the totals.
+// round(x * 2^40) to nearest (ties to even) as an int64, from the bits of
+// the float: exactly the value an FP64 multiply by 2^40 and conversion would
+// give (both are exact up to that one rounding), without the FP64 pipe.
+// Magnitudes of 2^23 and more saturate.
+__device__ __forceinline__ long long fix40(float x)
+{
+    const unsigned b = __float_as_uint(x);
+    const int e = (int)((b >> 23) & 0xffu);
+    if (e == 0) return 0;  // zero or subnormal: below 2^-126, rounds to 0
+    const int sh = e - 110;  // x * 2^40 = m * 2^(e - 127 - 23 + 40)
+    long long r;
+    if (sh > 39) {  // |x| >= 2^23: beyond int64
+        r = LLONG_MAX;
+    } else if (sh >= 0) {
+        r = (long long)(((unsigned long long)((b & 0x7fffffu) | 0x800000u)) << sh);
+    } else if (sh > -26) {
+        const unsigned long long m = (b & 0x7fffffu) | 0x800000u;
+        const int s = -sh;
+        unsigned long long q = m >> s;
+        const unsigned long long rem = m & ((1ull << s) - 1ull), half = 1ull << (s - 1);
+        q += (rem > half || (rem == half && (q & 1ull))) ? 1ull : 0ull;
+        r = (long long)q;
+    } else {
+        r = 0;  // below 2^-41
+    }
+    return (b >> 31) ? -r : r;
+}
+
+// Points [beg, end) of this block: n split into gridDim.x contiguous ranges
+// of n / G or n / G + 1 points, with 32-bit arithmetic (a 64-bit division
+// would run through the FP64 pipe).
+__device__ __forceinline__ void block_range(int n, long long& beg, long long& end)
+{
+    const unsigned G = gridDim.x, b = blockIdx.x, un = (unsigned)n;
+    const unsigned q = un / G, r = un % G;
+    beg = (long long)b * q + (b < r ? b : r);
+    end = beg + q + (b < r ? 1 : 0);
+}
+
+// Warps' partial sums (shared sh[warp * NV + i]) to block totals out[i]:
+// thread i adds value i over the warps in order, in FP64.
 template <int NV>
-__device__ inline void block_sum(double* v, double* sh)
+__device__ inline void warps_to_block(const double* sh, double* out)
+{
+    const int tid = threadIdx.x;
+    if (tid < NV) {
+        double s = 0.0;
+        for (int w = 0; w < AL_THREADS / 32; ++w) s += sh[w * NV + tid];
+        out[tid] = s;
+    }
+    __syncthreads();
+}
+
+// Fixed-order block sum of NV floats per thread, each lane's value carried
+// as an unevaluated float pair (s, c) through the warp's shuffle tree with
+// error-free additions (TwoSum), so the warp sum keeps about twice float
+// precision without the FP64 pipe; warps are then summed in FP64.
+// Block totals in out[0 .. NV) (shared), visible to every thread.
+template <int NV>
+__device__ inline void block_sum_ff(const float* v, double* sh, double* out)
 {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    float sv[NV], cv[NV];
+#pragma unroll
+    for (int i = 0; i < NV; ++i) {
+        sv[i] = v[i];
+        cv[i] = 0.0f;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+        for (int i = 0; i < NV; ++i) {
+            const float s2 = __shfl_xor_sync(0xffffffffu, sv[i], o), c2 = __shfl_xor_sync(0xffffffffu, cv[i], o);
+            // the same operand order on both lanes of a pair (lower lane's
+            // value first), so both hold bit-identical results
+            const bool low = (lane & o) == 0;
+            const float a = low ? sv[i] : s2, b = low ? s2 : sv[i];
+            const float ca = low ? cv[i] : c2, cb = low ? c2 : cv[i];
+            const float h = __fadd_rn(a, b);
+            const float bb = __fsub_rn(h, a);
+            const float err = __fadd_rn(__fsub_rn(a, __fsub_rn(h, bb)), __fsub_rn(b, bb));
+            sv[i] = h;
+            cv[i] = __fadd_rn(__fadd_rn(ca, cb), err);
+        }
+    if (lane == 0)
+        for (int i = 0; i < NV; ++i) sh[warp * NV + i] = (double)sv[i] + (double)cv[i];
+    __syncthreads();
+    warps_to_block<NV>(sh, out);
+}
+
+// Fixed-order block sum of NV floats per thread: the 32 lanes of a warp in
+// float (about one sample per lane in the polish, so float keeps ~1e-6 of
+// the sum), the warps and thread 0's totals in FP64 (out[0 .. NV)).
+template <int NV>
+__device__ inline void block_sum_f(float* v, double* sh, double* out)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
     for (int i = 0; i < NV; ++i)
         for (int o = 16; o > 0; o >>= 1) v[i] += __shfl_xor_sync(0xffffffffu, v[i], o);
     if (lane == 0)
-        for (int i = 0; i < NV; ++i) sh[warp * NV + i] = v[i];
+        for (int i = 0; i < NV; ++i) sh[warp * NV + i] = (double)v[i];
     __syncthreads();
-    if (tid == 0)
-        for (int i = 0; i < NV; ++i) {
-            double s = 0.0;
-            for (int w = 0; w < AL_THREADS / 32; ++w) s += sh[w * NV + i];
-            v[i] = s;
-        }
+    warps_to_block<NV>(sh, out);
 }
 
 // ---------------------------------------------------------------------------
@@ -276,32 +396,44 @@ struct AlignArgs {
     const double* dloss;  // F or null
     double* part;         // F x tiles x 8
     long long* acc;       // n_nodes or null
+    const FramePose* fposes;  // F, from align_prep
 };
+
+// Thread f prepares frame f: its perturbed pose, v and 2 W.
+__global__ void align_prep(const double* poses, const double* xi, const double* dloss, GridInfo g, int F,
+                           FramePose* out)
+{
+    const int f = blockIdx.x * blockDim.x + threadIdx.x;
+    if (f >= F) return;
+    double x[6] = {0, 0, 0, 0, 0, 0};
+    if (xi)
+        for (int i = 0; i < 6; ++i) x[i] = xi[6 * (size_t)f + i];
+    double T[12];
+    perturb(poses + 16 * (size_t)f, x, T);
+    FramePose fp;
+    make_posef(T, g, fp.P);
+    for (int i = 0; i < 3; ++i) fp.V[i] = (float)x[3 + i];
+    fp.w2 = (float)(2.0 * (dloss ? dloss[f] : 1.0));
+    out[f] = fp;
+}
 
 template <typename TS>
 __global__ void __launch_bounds__(AL_THREADS) align_kernel(AlignArgs a)
 {
-    __shared__ PoseF sP;
-    __shared__ float sV[3];
-    __shared__ double sW;
+    __shared__ FramePose sF;
     __shared__ double sh[(AL_THREADS / 32) * 8];
     const int f = blockIdx.y, tid = threadIdx.x;
-    if (tid == 0) {
-        double xi[6] = {0, 0, 0, 0, 0, 0};
-        if (a.xi)
-            for (int i = 0; i < 6; ++i) xi[i] = a.xi[6 * (size_t)f + i];
-        double T[12];
-        perturb(a.poses + 16 * (size_t)f, xi, T);
-        make_posef(T, a.g, sP);
-        for (int i = 0; i < 3; ++i) sV[i] = (float)xi[3 + i];
-        sW = a.dloss ? a.dloss[f] : 1.0;
-    }
-    __syncthreads();
+    block_copy_words(a.fposes + f, &sF);
+    const PoseF& sP = sF.P;
+    const float* sV = sF.V;
     const int n = a.counts ? min(a.counts[f], a.n_max) : a.n_max;
-    const long long beg = (long long)n * blockIdx.x / gridDim.x, end = (long long)n * (blockIdx.x + 1) / gridDim.x;
+    long long beg, end;
+    block_range(n, beg, end);
     const TS* tsdf = static_cast<const TS*>(a.tsdf);
     const float inv_vs = (float)a.g.inv_vs;
-    const double scale = 2.0 * sW * kFix;
+    // dL/dV increments in units of 2^-40: round(2 W t w 2^40), formed in
+    // float (exact for W = 1, one float rounding otherwise)
+    const float w2 = sF.w2;
     float acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};  // L, C, gw[3], gv[3]
     for (long long e = beg + tid; e < end; e += AL_THREADS) {
         const float4 p = __ldg(a.pts + (size_t)f * a.n_max + e);
@@ -328,19 +460,14 @@ __global__ void __launch_bounds__(AL_THREADS) align_kernel(AlignArgs a)
                 const float w = ((c & 1) ? fr[0] : 1.0f - fr[0]) * (((c >> 1) & 1) ? fr[1] : 1.0f - fr[1]) *
                                 (((c >> 2) & 1) ? fr[2] : 1.0f - fr[2]);
                 const long long idx = base + ((c & 1) ? 1 : 0) + (((c >> 1) & 1) ? nx : 0) + (((c >> 2) & 1) ? nxy : 0);
-                const long long inc = __double2ll_rn(scale * (double)(t * w));
+                const long long inc = fix40(w2 * (t * w));
                 if (inc != 0) atomicAdd(reinterpret_cast<unsigned long long*>(a.acc + idx), (unsigned long long)inc);
             }
         }
     }
-    double dacc[8];
-#pragma unroll
-    for (int i = 0; i < 8; ++i) dacc[i] = (double)acc[i];
-    block_sum<8>(dacc, sh);
-    if (tid == 0) {
-        double* out = a.part + ((size_t)f * gridDim.x + blockIdx.x) * 8;
-        for (int i = 0; i < 8; ++i) out[i] = dacc[i];
-    }
+    __shared__ double tot[8];
+    block_sum_ff<8>(acc, sh, tot);
+    if (tid < 8) a.part[((size_t)f * gridDim.x + blockIdx.x) * 8 + tid] = tot[tid];
 }
 
 // Sums of NV values over `tiles` partial records (record y at part + y *
@@ -392,10 +519,35 @@ __global__ void __launch_bounds__(RED_THREADS) align_finish(const double* part, 
     }
 }
 
+// v * 2^-40 rounded to the nearest float (ties to even), by integer
+// operations: the same float as the FP64 conversion and multiply for |v| <
+// 2^53, without the FP64 pipe (v * 2^-40 stays inside the normal floats).
+__device__ __forceinline__ float fixed40_to_float(long long v)
+{
+    if (v == 0) return 0.0f;
+    const unsigned long long m = v < 0 ? 0ull - (unsigned long long)v : (unsigned long long)v;
+    const int msb = 63 - __clzll((long long)m);
+    int e = msb - 40;
+    unsigned long long q;
+    if (msb <= 23) {
+        q = m << (23 - msb);
+    } else {
+        const int s = msb - 23;
+        q = m >> s;
+        const unsigned long long rem = m & ((1ull << s) - 1ull), half = 1ull << (s - 1);
+        q += (rem > half || (rem == half && (q & 1ull))) ? 1ull : 0ull;
+        if (q == (1ull << 24)) {
+            q >>= 1;
+            ++e;
+        }
+    }
+    return __uint_as_float((v < 0 ? 0x80000000u : 0u) | ((unsigned)(e + 127) << 23) | ((unsigned)q & 0x7fffffu));
+}
+
 __global__ void fixed_to_float(const long long* acc, float* out, size_t n)
 {
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
-        out[i] = (float)((double)acc[i] * (1.0 / kFix));
+        out[i] = fixed40_to_float(acc[i]);
 }
 
 // ---------------------------------------------------------------------------
@@ -408,24 +560,21 @@ struct GnArgs {
     const int* n_dev;
     int n_max;
     GnState* st;
-    double* part;  // tiles x GN_VALS
+    double* part;      // tiles x GN_VALS
+    const PoseF* pc;   // the candidate prepared by gn_begin / gn_step
 };
 
 template <typename TS>
 __global__ void __launch_bounds__(AL_THREADS) gn_kernel(GnArgs a)
 {
     __shared__ PoseF sP;
-    __shared__ int sGo;
     __shared__ double sh[(AL_THREADS / 32) * GN_VALS];
     const int tid = threadIdx.x;
-    if (tid == 0) {
-        sGo = a.st->have_cand;
-        if (sGo) make_posef(a.st->Tc, a.g, sP);
-    }
-    __syncthreads();
-    if (!sGo) return;  // no candidate this step: gn_step ignores the partials
+    if (!a.st->have_cand) return;  // no candidate this step: gn_step ignores the partials
+    block_copy_words(a.pc, &sP);
     const int n = a.n_dev ? min(*a.n_dev, a.n_max) : a.n_max;
-    const long long beg = (long long)n * blockIdx.x / gridDim.x, end = (long long)n * (blockIdx.x + 1) / gridDim.x;
+    long long beg, end;
+    block_range(n, beg, end);
     const TS* tsdf = static_cast<const TS*>(a.tsdf);
     const float inv_vs = (float)a.g.inv_vs;
     float acc[GN_VALS];
@@ -454,12 +603,9 @@ __global__ void __launch_bounds__(AL_THREADS) gn_kernel(GnArgs a)
         acc[27] = fmaf(t, t, acc[27]);
         acc[28] += 1.0f;
     }
-    double dacc[GN_VALS];
-#pragma unroll
-    for (int i = 0; i < GN_VALS; ++i) dacc[i] = (double)acc[i];
-    block_sum<GN_VALS>(dacc, sh);
-    if (tid == 0)
-        for (int i = 0; i < GN_VALS; ++i) a.part[(size_t)blockIdx.x * GN_VALS + i] = dacc[i];
+    __shared__ double tot[GN_VALS];
+    block_sum_f<GN_VALS>(acc, sh, tot);
+    if (tid < GN_VALS) a.part[(size_t)blockIdx.x * GN_VALS + tid] = tot[tid];
 }
 
 // solve the 6x6 system A d = y by Gaussian elimination with partial pivoting
@@ -495,10 +641,11 @@ __device__ inline bool solve6(double* A, double* y, double d[6])
 }
 
 // The input pose becomes the first candidate to evaluate.
-__global__ void gn_begin(GnState* st, const double* pose_in)
+__global__ void gn_begin(GnState* st, const double* pose_in, GridInfo g, PoseF* pc)
 {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
     for (int i = 0; i < 12; ++i) st->Tc[i] = pose_in[i];
+    make_posef(st->Tc, g, *pc);
     st->lambda = 1e-3;
     st->accepted = 0;
     st->step = 0;
@@ -510,7 +657,8 @@ __global__ void gn_begin(GnState* st, const double* pose_in)
 // step (accept or drop the evaluated candidate).  Then form the next
 // candidate.
 __global__ void __launch_bounds__(RED_THREADS) gn_step(GnState* st, const double* part, int tiles, int mode,
-                                                       double* pose_out, double* trace, int* accepted_out)
+                                                       double* pose_out, double* trace, int* accepted_out,
+                                                       GridInfo g, PoseF* pc)
 {
     __shared__ double sh[RED_THREADS];
     __shared__ double s[GN_VALS];
@@ -551,6 +699,7 @@ __global__ void __launch_bounds__(RED_THREADS) gn_step(GnState* st, const double
         }
         if (solve6(A, y, d)) {
             perturb(st->T, d, st->Tc);
+            make_posef(st->Tc, g, *pc);
             st->have_cand = 1;
         }
     }
@@ -613,6 +762,8 @@ void align_release(const pf_volume* v)
     cudaFree(it->second.acc);
     cudaFree(it->second.gn_part);
     cudaFree(it->second.gn_state);
+    cudaFree(it->second.frame_pose);
+    cudaFree(it->second.gn_pose);
     g_scratch.erase(it);
 }
 }  // namespace pf
@@ -637,6 +788,13 @@ pf_status pf_align_loss(const pf_volume* v, const float* points_dev, const int* 
         PF_CUDA(cudaMalloc(&sc.part, need * sizeof(double)));
         sc.part_cap = need;
     }
+    if (sc.frame_cap < n_frames) {
+        cudaFree(sc.frame_pose);
+        sc.frame_pose = nullptr;
+        sc.frame_cap = 0;
+        PF_CUDA(cudaMalloc(&sc.frame_pose, (size_t)n_frames * sizeof(FramePose)));
+        sc.frame_cap = n_frames;
+    }
     if (grad_tsdf_dev && !sc.acc) PF_CUDA(cudaMalloc(&sc.acc, v->n_nodes * sizeof(long long)));
     if (grad_tsdf_dev) PF_CUDA(cudaMemsetAsync(sc.acc, 0, v->n_nodes * sizeof(long long), s));
     AlignArgs a;
@@ -650,8 +808,11 @@ pf_status pf_align_loss(const pf_volume* v, const float* points_dev, const int* 
     a.dloss = dloss_dev;
     a.part = sc.part;
     a.acc = grad_tsdf_dev ? sc.acc : nullptr;
+    a.fposes = static_cast<const FramePose*>(sc.frame_pose);
+    align_prep<<<(n_frames + 63) / 64, 64, 0, s>>>(poses_dev, xi_dev, dloss_dev, a.g, n_frames,
+                                                   static_cast<FramePose*>(sc.frame_pose));
     launch_storage<AlignLaunch>(v, dim3(tiles, n_frames), s, a);
-    pf::count_launch();
+    pf::count_launch(2);
     PF_LAUNCHED();
     align_finish<<<n_frames, RED_THREADS, 0, s>>>(sc.part, tiles, xi_dev, dloss_dev, loss_dev, count_dev,
                                                   grad_xi_dev);
@@ -675,6 +836,8 @@ pf_status pf_polish(const pf_volume* v, const float* points_dev, const int* n_de
     AlignScratch& sc = scratch_of(v);
     if (!sc.gn_part) PF_CUDA(cudaMalloc(&sc.gn_part, (size_t)AL_TILES * GN_VALS * sizeof(double)));
     if (!sc.gn_state) PF_CUDA(cudaMalloc(&sc.gn_state, sizeof(GnState)));
+    if (!sc.gn_pose) PF_CUDA(cudaMalloc(&sc.gn_pose, sizeof(PoseF)));
+    PoseF* pc = static_cast<PoseF*>(sc.gn_pose);
     GnState* st = reinterpret_cast<GnState*>(sc.gn_state);
 
     GnArgs a;
@@ -685,17 +848,18 @@ pf_status pf_polish(const pf_volume* v, const float* points_dev, const int* n_de
     a.n_max = n_max;
     a.st = st;
     a.part = sc.gn_part;
+    a.pc = pc;
     // evaluate the input pose, then `steps` candidates
-    gn_begin<<<1, 1, 0, s>>>(st, pose_dev);
+    gn_begin<<<1, 1, 0, s>>>(st, pose_dev, a.g, pc);
     launch_storage<GnLaunch>(v, dim3(AL_TILES), s, a);
     gn_step<<<1, RED_THREADS, 0, s>>>(st, sc.gn_part, AL_TILES, 0, steps == 0 ? pose_dev : nullptr, trace_dev,
-                                      accepted_dev);
+                                      accepted_dev, a.g, pc);
     pf::count_launch(3);
     PF_LAUNCHED();
     for (int k = 0; k < steps; ++k) {
         launch_storage<GnLaunch>(v, dim3(AL_TILES), s, a);
         gn_step<<<1, RED_THREADS, 0, s>>>(st, sc.gn_part, AL_TILES, 1, k == steps - 1 ? pose_dev : nullptr,
-                                          trace_dev, accepted_dev);
+                                          trace_dev, accepted_dev, a.g, pc);
         pf::count_launch(2);
         PF_LAUNCHED();
     }
