@@ -440,7 +440,8 @@ def run_ours(args):
         "fitness_vs_plain": vs_plain,
         "roofline": {"bound": "alu", "kernel": "fitness_kernel<search>", "achieved": achieved_tflops,
                      "peak": peak_tflops, "unit": "TFLOP/s", "frac": achieved_tflops / peak_tflops,
-                     "traffic": committed_traffic(), "avg_launch_ms": fit_avg_ms, "launches": fit_n,
+                     "traffic": committed_traffic(), "binding_unit": committed_l1_pipe(),
+                     "avg_launch_ms": fit_avg_ms, "launches": fit_n,
                      "flop_per_sample": FLOP_PER_SAMPLE, "samples_per_launch": samples_per_launch,
                      "peak_source": "FP32 lanes x clock: 152 SMs x 128 x 2 flop x 2070 MHz (derived)"},
         "kernel_ms": {cls: {"total_ms": v[0], "launches": v[1]} for cls, v in kt.items()},
@@ -486,6 +487,26 @@ def committed_traffic():
     if not m or not h or h.group(1) != sha:
         return None
     return int(m.group(1))
+
+
+def committed_l1_pipe():
+    """The unit that bounds the fitness kernel, from the same committed ncu
+    summary: L1 data-pipe wavefronts as a fraction of peak in each lane
+    mapping (None when the kernel's sources have changed since)."""
+    import re
+    path = os.path.join(ROOT, "profiles", "fitness_kernel_multiroom.md")
+    try:
+        text = open(path).read()
+        sha = fitness_source_sha()
+    except OSError:
+        return None
+    h = re.search(r"kernel_source_sha256_prefix:\s*([0-9a-f]+)", text)
+    a = re.search(r"l1_data_pipe_frac_points_on_lanes:\s*([0-9.]+)", text)
+    b = re.search(r"l1_data_pipe_frac_particles_on_lanes:\s*([0-9.]+)", text)
+    if not h or h.group(1) != sha or not a or not b:
+        return None
+    return {"unit": "L1 data-pipe wavefronts, fraction of peak (ncu)", "points_on_lanes": float(a.group(1)),
+            "particles_on_lanes": float(b.group(1)), "source": "profiles/fitness_kernel_multiroom.md"}
 
 
 def fp32_peak_tflops() -> float:
