@@ -639,7 +639,7 @@ def test_raycast_recovers_the_analytic_depth(with_spheres):
     depth, normals = _orc().raycast(vol, intr, P)
     hit = depth > 0
     # pixels near the border look through parts of the band whose nodes
-    # project outside every fused image; judge the interior
+    # project outside every fused image; check the interior
     inner = np.zeros_like(hit)
     inner[3:-3, 3:-3] = True
     assert np.count_nonzero(hit & inner) > 0.9 * np.count_nonzero(inner)
