@@ -220,3 +220,85 @@ def test_autotune_and_validation(pf):
     v16 = pf.Volume.from_grid(SEQS[0][0], tsdf_dtype=pf.PF_F16)
     with pytest.raises(pf.ProfusionError):
         pf.Batch([vols[0], v16], [SEQS[0][1]] * 2, params[:2])
+
+
+# Closed loop over the multiroom trajectory, with camera / volume / particle
+# mixes from the small end of the batch workload: (camera, nodes per axis over
+# the 5.12 m scene, seed, particles).
+TRAJ = [((160, 120), 128, 0, 1024), ((320, 240), 128, 1, 2048), ((160, 120), 256, 2, 1024)]
+TRAJ_FRAMES = 4
+_TRAJ_ORACLE = {}
+
+
+def _traj_sequence(res, n, seed):
+    w, h = res
+    f = 525.0 * w / 640.0
+    intr = Intrinsics(w, h, f, f, (w - 1) / 2.0, (h - 1) / 2.0, 0.1, 8.0)
+    vs = 5.12 / n
+    return synth.multiroom_sequence(300, seed, grid=Grid(n, n, n, vs, 3.0 * vs, (0.0, 0.0, 0.0)), intr=intr)
+
+
+def _traj_params(K):
+    return dict(n_iters=20, k_sched=(K, K, K), decim_sched=(1, 1, 1), update_mode=0, compose_mode=1,
+                min_valid_frac=0.05)
+
+
+def _oracle_trajectory(i):
+    """The FP64 oracle's closed loop for sequence i: frame 0 fused at its true
+    pose, then per frame P0 = P_prev @ perturbed relative pose, search, and
+    fusion at the pose found."""
+    if i not in _TRAJ_ORACLE:
+        res, n, seed, K = TRAJ[i]
+        seq = _traj_sequence(res, n, seed)
+        ovol = oracle.Volume(abi(seq.grid))
+        intr = abi(seq.intr)
+        oracle.integrate(ovol, seq.depth(0), intr, seq.gt[0])
+        poses = [seq.gt[0]]
+        prm = oracle.TrackParams(**_traj_params(K))
+        for f in range(1, TRAJ_FRAMES + 1):
+            r = oracle.track(ovol, seq.depth(f), intr, synth.templates(2048, 0), poses[-1] @ seq.relative_init(f), prm)
+            poses.append(r.pose)
+            oracle.integrate(ovol, seq.depth(f), intr, r.pose)
+        _TRAJ_ORACLE[i] = np.array(poses)
+    return _TRAJ_ORACLE[i]
+
+
+@pytest.mark.parametrize("storage", ["f32", "bf16"])
+def test_batched_trajectory_stays_with_the_oracle(pf, storage):
+    """Three sequences stepped as one batch under a CUDA graph for four
+    frames, each frame tracked from the previous frame's result and fused at
+    the pose found, against the oracle's FP64 closed loop on its own FP64
+    grid.  Float storage: every frame within 1e-4 m and 1e-4 rad of the
+    oracle.  bfloat16 storage with uint8 weights: the first frame within 1 mm
+    (from then on the two grids differ by the storage's rounding, which can
+    tip later decisions of the search)."""
+    torch = torch_cuda()
+    seqs = [_traj_sequence(res, n, seed) for res, n, seed, _ in TRAJ]
+    dtype, u8 = (pf.PF_F32, 0) if storage == "f32" else (pf.PF_BF16, 1)
+    vols = [pf.Volume.from_grid(s.grid, tsdf_dtype=dtype, weight_u8=u8) for s in seqs]
+    templ = torch.from_numpy(synth.templates(2048, 0)).cuda()
+    params = [pf.track_params(templ, **_traj_params(K)) for *_, K in TRAJ]
+    batch = pf.Batch(vols, [s.intr for s in seqs], params, use_graph=True)
+    for i, s in enumerate(seqs):
+        batch.pose[i].copy_(to_dev(s.gt[0]))
+        batch.depth[i].copy_(to_dev(s.depth(0)))
+    batch.fuse()
+    n_frames = TRAJ_FRAMES if storage == "f32" else 1
+    gpu = np.zeros((len(seqs), n_frames + 1, 4, 4))
+    for f in range(1, n_frames + 1):
+        for i, s in enumerate(seqs):
+            batch.depth[i].copy_(to_dev(s.depth(f)))
+            batch.rel[i].copy_(to_dev(s.relative_init(f)))
+        batch.step()
+        torch.cuda.synchronize()
+        for i in range(len(seqs)):
+            gpu[i, f] = batch.pose[i].cpu().numpy()
+    batch.close()
+    for i in range(len(seqs)):
+        ref = _oracle_trajectory(i)
+        for f in range(1, n_frames + 1):
+            if storage == "f32":
+                assert pose_trans_err(gpu[i, f], ref[f]) <= 1e-4, (i, f)
+                assert pose_rot_err(gpu[i, f], ref[f]) <= 1e-4, (i, f)
+            else:
+                assert pose_trans_err(gpu[i, f], ref[f]) <= 1e-3, (i, f)
