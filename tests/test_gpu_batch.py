@@ -263,18 +263,18 @@ def _oracle_trajectory(i):
     return _TRAJ_ORACLE[i]
 
 
-@pytest.mark.parametrize("storage", ["f32", "bf16"])
+@pytest.mark.parametrize("storage", ["f32", "f16", "bf16"])
 def test_batched_trajectory_stays_with_the_oracle(pf, storage):
     """Three sequences stepped as one batch under a CUDA graph for four
     frames, each frame tracked from the previous frame's result and fused at
     the pose found, against the oracle's FP64 closed loop on its own FP64
     grid.  Float storage: every frame within 1e-4 m and 1e-4 rad of the
-    oracle.  bfloat16 storage with uint8 weights: the first frame within 1 mm
-    (from then on the two grids differ by the storage's rounding, which can
-    tip later decisions of the search)."""
+    oracle.  half or bfloat16 storage with uint8 weights: the first frame
+    within 1 mm (from then on the two grids differ by the storage's
+    rounding, which can tip later decisions of the search)."""
     torch = torch_cuda()
     seqs = [_traj_sequence(res, n, seed) for res, n, seed, _ in TRAJ]
-    dtype, u8 = (pf.PF_F32, 0) if storage == "f32" else (pf.PF_BF16, 1)
+    dtype, u8 = {"f32": (pf.PF_F32, 0), "f16": (pf.PF_F16, 1), "bf16": (pf.PF_BF16, 1)}[storage]
     vols = [pf.Volume.from_grid(s.grid, tsdf_dtype=dtype, weight_u8=u8) for s in seqs]
     templ = torch.from_numpy(synth.templates(2048, 0)).cuda()
     params = [pf.track_params(templ, **_traj_params(K)) for *_, K in TRAJ]
