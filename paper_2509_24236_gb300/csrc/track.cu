@@ -741,6 +741,36 @@ __device__ inline void argmin_pair(float& e, int& k, float* se, int* sk)
 #define PF_FIT_MIN_BLOCKS 3
 #endif
 
+// Sums of one particle's partials over the point tiles, S = sum of
+// part_S[y K + k] and C likewise for y = 0, 1, ..., T - 1 in that order.
+// The loads go out 16 at a time before they are added (in the same order),
+// so the last CTA waits one L2 round trip per 16 tiles instead of a few per
+// tile.  Adding 0 for the padding slots leaves the float sum unchanged (the
+// partial sums are non-negative), so the result is that of the plain loop.
+__device__ __forceinline__ void sum_tiles(const float* part_S, const int* part_C, int K, int T, int k, float& S,
+                                          int& C)
+{
+    constexpr int B = 16;
+    S = 0.0f;
+    C = 0;
+    for (int y0 = 0; y0 < T; y0 += B) {
+        float sv[B];
+        int cv[B];
+#pragma unroll
+        for (int q = 0; q < B; ++q) {
+            const bool in = y0 + q < T;
+            const size_t o = (size_t)(in ? y0 + q : y0) * K + k;
+            sv[q] = in ? __ldcg(part_S + o) : 0.0f;
+            cv[q] = in ? __ldcg(part_C + o) : 0;
+        }
+#pragma unroll
+        for (int q = 0; q < B; ++q) {
+            S += sv[q];
+            C += cv[q];
+        }
+    }
+}
+
 // The work of one CTA: particle chunk bx, point tile by, of a launch of
 // n_blocks CTAs for this problem (the last of them to finish runs the
 // epilogue).
@@ -1111,13 +1141,9 @@ __device__ __forceinline__ void fitness_body(const FitArgs& a, int bx, int by, u
     // ------------------------------------------------------------------
     if (SRC == SRC_POSES) {
         for (int k = tid; k < a.K; k += FIT_THREADS) {
-            float S = 0.0f;
-            int C = 0;
-#pragma unroll 4
-            for (int y = 0; y < a.n_ptiles; ++y) {
-                S += __ldcg(a.part_S + (size_t)y * a.K + k);
-                C += __ldcg(a.part_C + (size_t)y * a.K + k);
-            }
+            float S;
+            int C;
+            sum_tiles(a.part_S, a.part_C, a.K, a.n_ptiles, k, S, C);
             a.out_E[k] = C > 0 ? __fdiv_rn(S, (float)C) : INFINITY;
             a.out_C[k] = C;
         }
@@ -1166,12 +1192,9 @@ __device__ __forceinline__ void fitness_body(const FitArgs& a, int bx, int by, u
         __shared__ int sn[FIT_WARPS];
         SearchState* st = a.st;
         if (tid == 0) {
-            float S = 0.0f;
-            int C = 0;
-            for (int y = 0; y < a.n_ptiles; ++y) {
-                S += __ldcg(a.part_S + (size_t)y * a.K);
-                C += __ldcg(a.part_C + (size_t)y * a.K);
-            }
+            float S;
+            int C;
+            sum_tiles(a.part_S, a.part_C, a.K, a.n_ptiles, 0, S, C);
             s_E0 = C > 0 ? __fdiv_rn(S, (float)C) : INFINITY;
             s_C0 = C;
         }
@@ -1182,13 +1205,9 @@ __device__ __forceinline__ void fitness_body(const FitArgs& a, int bx, int by, u
         int nadv = 0;
         double sum[6] = {0, 0, 0, 0, 0, 0};
         for (int k = tid; k < a.K; k += FIT_THREADS) {
-            float S = 0.0f;
-            int C = 0;
-#pragma unroll 4
-            for (int y = 0; y < a.n_ptiles; ++y) {
-                S += __ldcg(a.part_S + (size_t)y * a.K + k);
-                C += __ldcg(a.part_C + (size_t)y * a.K + k);
-            }
+            float S;
+            int C;
+            sum_tiles(a.part_S, a.part_C, a.K, a.n_ptiles, k, S, C);
             const float E = C > 0 ? __fdiv_rn(S, (float)C) : INFINITY;
             if (E < be) {
                 be = E;
