@@ -657,3 +657,33 @@ def test_raycast_recovers_the_analytic_depth(with_spheres):
         # wall normals are the axis directions
         n = normals[ok & inner]
         assert np.mean(np.max(np.abs(n), axis=-1) > 0.97) > 0.9
+
+
+def test_fusion_of_a_tiny_grid_matches_the_hand_worked_example():
+    """4^3 nodes, a 3x3 image, two views (constant depth, then depth that
+    differs by image column, so that the nearest-pixel rounding decides
+    values): every node's tsdf and weight after each view, worked by hand
+    from the fusion rule (fixture tests/golden/fusion_tiny_grid.json, with
+    its derivation)."""
+    with open(os.path.join(os.path.dirname(__file__), "golden", "fusion_tiny_grid.json")) as fh:
+        fx = json.load(fh)
+    g, c = fx["grid"], fx["camera"]
+    grid = synth.Grid(*g["n"], g["voxel"], g["trunc"], tuple(g["origin"]))
+    intr = synth.Intrinsics(c["width"], c["height"], c["fx"], c["fy"], c["cx"], c["cy"], c["depth_min"], c["depth_max"])
+    vol = _orc().Volume(grid)
+    for row, exp in zip(fx["depth_rows"], fx["expected"]):
+        depth = np.tile(np.asarray(row, dtype=np.float32), (3, 1))   # the same depth in every image row
+        _orc().integrate(vol, depth, intr, np.eye(4))
+        tsdf = vol.tsdf.reshape(4, 4, 4)      # [k, j, i]: x fastest
+        weight = vol.weight.reshape(4, 4, 4)
+        for k in range(4):
+            e = exp[f"k{k}"]
+            mask = np.zeros((4, 4), dtype=bool)  # [j, i]
+            if e["ij"] == "all":
+                mask[:] = True
+            for i, j in ([] if e["ij"] == "all" else e["ij"]):
+                mask[j, i] = True
+            want = np.array([num / den for num, den in e["tsdf_by_i"]])[None, :].repeat(4, axis=0)
+            assert np.all(weight[k][mask] == e["weight"]), (row, k)
+            assert np.allclose(tsdf[k][mask], want[mask], rtol=0, atol=1e-12), (row, k)
+            assert np.all(weight[k][~mask] == 0) and np.all(tsdf[k][~mask] == 1.0), (row, k)
