@@ -80,6 +80,12 @@ def parse():
                          "seeds 0-9) with each layout, and the oracle on the host; precision: 640x480 into 768^3 at "
                          "8 mm with f32 / f16 / bf16 tsdf and uint8 weights -- fusion at the true poses (TSDF "
                          "deviation from the f32 volume) and tracking (frames/s, ATE), over --steps frames")
+    ap.add_argument("--frames", type=int, default=300,
+                    help="--kernel precision: length of the multiroom trajectory (30 Hz); --steps + 1 frames of it "
+                         "are used")
+    ap.add_argument("--fusion-only", action="store_true",
+                    help="--kernel precision: fuse every frame at its true pose and report the storage deviation "
+                         "only (no tracking pass)")
     ap.add_argument("--spread", type=float, default=3.0,
                     help="--kernel fitness: poses perturbed up to this many degrees and centimetres")
     ap.add_argument("--reps", type=int, default=3, help="--kernel: timed launches after one warm-up launch")
@@ -964,12 +970,13 @@ def run_precision(args):
     trajectory and the f32 one."""
     import synth
     n = max(2, args.steps + 1)
+    n_traj = max(args.frames, n)
     grid = synth.Grid(768, 768, 768, 0.008, 0.024, (-0.5, -0.5, -0.5))
-    seq = synth.multiroom_sequence(300, args.seed, grid=grid)
+    seq = synth.multiroom_sequence(n_traj, args.seed, grid=grid)
     depths, rels = [], []
     import multiprocessing as mp
     with mp.get_context("spawn").Pool(max(1, min(16, (os.cpu_count() or 2) - 1))) as pool:
-        out = pool.map(_render, [(300, args.seed, f, 1) for f in range(n)])
+        out = pool.map(_render, [(n_traj, args.seed, f, 1) for f in range(n)])
     depths = [o[0] for o in out]
     rels = [o[1] for o in out]
     import torch
@@ -1003,6 +1010,10 @@ def run_precision(args):
             r["tsdf_vs_f32"] = {"rms": float(np.sqrt(np.mean(diff ** 2))), "max": float(diff.max()),
                                 "nodes": int(both.sum()), "weights_equal": bool(np.array_equal(w, ref_w))}
         del t, w
+        if args.fusion_only:
+            res[name + "+u8" + ("+narrow" if view == 2 else "")] = r
+            vol.close()
+            continue
         vol.reset()
         pose = torch.zeros((n, 16), dtype=torch.float64, device=dev)
         init = torch.zeros_like(pose)
@@ -1029,8 +1040,10 @@ def run_precision(args):
                                                                                        axis=1)))
         res[name + "+u8" + ("+narrow" if view == 2 else "")] = r
         vol.close()
-    print(json.dumps({"kernel": "precision", "workload": f"multiroom 640x480, {n - 1} tracked frames, 768^3 TSDF @ "
-                      "8 mm (tau 2.4 cm), 3072 particles x 20 iterations, uint8 weights", "results": res}))
+    what = f"{n} frames fused at their true poses" if args.fusion_only else f"{n - 1} tracked frames"
+    print(json.dumps({"kernel": "precision", "workload": f"multiroom 640x480 ({n_traj}-frame trajectory), {what}, "
+                      "768^3 TSDF @ 8 mm (tau 2.4 cm), 3072 particles x 20 iterations, uint8 weights",
+                      "results": res}))
     return 0
 
 
