@@ -137,3 +137,48 @@ def test_polish_descends_towards_the_true_pose():
     # the true pose is a fixed point: no candidate improves it materially
     P2, _, tr2 = o.polish(vol, pts, fr.gt_pose, steps=3)
     assert np.linalg.norm(P2[:3, 3] - fr.gt_pose[:3, 3]) < 0.1 * synth.ROOM64_GRID.voxel_size
+
+
+def test_polish_damping_schedule_on_one_point_in_closed_form():
+    """The damped Gauss-Newton schedule (lambda_0 = 1e-3, / 10 on an accepted
+    step, x 10 on a rejected one, a candidate kept only if it lowers the mean
+    squared residual, an invalid candidate never) on one point of an affine
+    field f = a . X + b.  There H = J^T J has rank one, and the damped system
+    (J^T J + lambda diag(J^2)) d = -r J has the closed-form solution
+    d_i = -r / (J_i (lambda + 6)) (Sherman-Morrison; J = (q x a, a), every
+    component nonzero), so the whole accept / reject sequence follows by hand
+    from the step's closed form and Exp (scipy).  The field's zero level lies
+    outside the grid: undamped steps overshoot (larger residual) or leave
+    the grid (no valid cell), and the schedule has to raise lambda to 100
+    before it moves again."""
+    from scipy.spatial.transform import Rotation
+    o = _orc()
+    g = Grid(40, 40, 40, 0.05, 0.15, (-1.0, -1.0, -1.0))
+    a, b = np.array([0.15, -0.1, 0.2]), 0.5           # node values in (0.05, 0.94): all inside the band
+    X = g.node_positions().reshape(-1, 3)
+    vol = o.Volume(g, X @ a + b, np.ones(g.n_nodes))
+    q0 = np.array([0.12, 0.23, -0.09])
+
+    def inside(q):
+        gc = (q - np.array(g.origin)) / g.voxel_size
+        return bool(np.all((gc >= 0) & (gc < g.nx - 1)))
+
+    q, lam, r = q0.copy(), 1e-3, q0 @ a + b
+    obj, decisions, trace = r * r, "", [r * r]
+    for _ in range(14):
+        J = np.concatenate([np.cross(q, a), a])
+        d = -r / (J * (lam + 6.0))
+        qc = Rotation.from_rotvec(d[:3]).apply(q) + d[3:]
+        objc = (qc @ a + b) ** 2 if inside(qc) else np.inf
+        assert not np.isfinite(objc) or abs(objc - obj) > 1e-3 * obj   # clear decisions only
+        if objc < obj:
+            q, r, obj, lam, decisions = qc, qc @ a + b, objc, lam / 10, decisions + "A"
+        else:
+            lam, decisions = lam * 10, decisions + "R"
+        trace.append(obj)
+    # accepts, rejects by overshoot, by leaving the grid, lambda up to 100 and down again
+    assert decisions == "AARRRRRRRAARRR"
+    P, accepted, tr = o.polish(vol, q0[None, :], np.eye(4), steps=14)
+    assert accepted == decisions.count("A")
+    np.testing.assert_allclose(tr, trace, rtol=1e-8)
+    np.testing.assert_allclose(P[:3, :3] @ q0 + P[:3, 3], q, atol=1e-9)

@@ -488,6 +488,60 @@ def test_search_closed_form_on_a_linear_field_best_mode():
     assert np.allclose(res.pose[:3, 3], t, atol=1e-14)
 
 
+@pytest.mark.parametrize("compose_mode", [0, 1])
+def test_search_closed_form_with_rotations_on_a_linear_field(compose_mode):
+    """The rotation half of the advantage-set mean (Sec. III-B: rotations
+    averaged in SO(3), read as the arithmetic mean of the rotation vectors
+    then Exp): on a field f = a . X + b with every sample in the band, the
+    fitness of any pose is E(R, t) = a . (R xbar + t) + b (xbar = the mean
+    back-projected point), so the advantage set, its mean rotation vector and
+    translation, the composed pose and the search size follow in closed form
+    -- computed here with scipy's rotations, from the starting pose on."""
+    from scipy.spatial.transform import Rotation
+    g = Grid(40, 40, 40, 0.05, 0.15, (0.0, 0.0, 0.0))
+    a, b = np.array([0.15, -0.1, 0.12]), 0.3         # node values in (0.1, 0.83): all inside the band
+    vol = affine_volume(g, a, b)
+    intr = Intrinsics(8, 6, 8.0, 8.0, 3.5, 2.5, 0.1, 8.0)
+    depth = np.full((6, 8), 0.8, dtype=np.float32)
+    R0 = Rotation.from_rotvec([0.2, -0.3, 0.1]).as_matrix()
+    P0 = np.eye(4)
+    P0[:3, :3] = R0
+    P0[:3, 3] = [0.9, 1.0, 0.5]
+    templ = synth.templates(64, 23)
+    pts = _orc().backproject(depth, intr)
+    xbar = pts.mean(axis=0)
+    prm = _orc().TrackParams(n_iters=3, k_sched=(64, 64, 64), decim_sched=(1, 1, 1), s0_deg=8.0, s0_cm=5.0,
+                             update_mode=0, compose_mode=compose_mode)
+    res = _orc().track(vol, depth, intr, templ, P0, prm)
+    R, t, s = R0.copy(), P0[:3, 3].copy(), np.array([8.0, 5.0])
+    for it in range(3):
+        w = np.deg2rad(s[0]) * templ[:, :3].astype(np.float64)
+        dt = s[1] / 100 * templ[:, 3:].astype(np.float64)
+        dR = Rotation.from_rotvec(w).as_matrix()
+        Rk = dR @ R
+        tk = (dR @ t if compose_mode == 0 else np.broadcast_to(t, (64, 3))) + dt
+        for k in range(64):   # every sample of every particle lies inside the grid
+            gc = (pts @ Rk[k].T + tk[k]) / g.voxel_size
+            assert np.all((gc >= 0) & (gc < g.nx - 1))
+        E = (Rk @ xbar + tk) @ a + b
+        assert np.min(np.abs(E[1:] - E[0])) > 1e-5 * E[0]    # no decision within rounding of its threshold
+        adv = E[1:] < E[0]
+        assert res.stats["n_adv"][it] == np.count_nonzero(adv)
+        assert res.stats["E0"][it] == pytest.approx(E[0], rel=1e-12)
+        assert np.allclose(res.stats["s"][it], s, rtol=1e-14)
+        mu_w, mu_t = w[1:][adv].mean(axis=0), dt[1:][adv].mean(axis=0)
+        dRm = Rotation.from_rotvec(mu_w).as_matrix()
+        R_wrong = R @ dRm                                   # the mean applied on the other side
+        R, t = dRm @ R, (dRm @ t if compose_mode == 0 else t) + mu_t
+        E_new = (R @ xbar + t) @ a + b
+        assert res.stats["E_new"][it] == pytest.approx(E_new, rel=1e-12)
+        got = res.stats["pose"][it].reshape(3, 4)
+        assert np.max(np.abs(got[:, :3] - R)) < 1e-13 and np.max(np.abs(got[:, 3] - t)) < 1e-13
+        assert np.max(np.abs(got[:, :3] - R_wrong)) > 1e-3   # the pin tells the sides apart
+        s = (0.1 + 0.9 * E_new) * s
+    assert np.max(np.abs(res.pose[:3, :3] - R)) < 1e-13 and np.max(np.abs(res.pose[:3, 3] - t)) < 1e-13
+
+
 def test_search_size_closed_form_on_a_constant_field():
     g = Grid(30, 30, 30, 0.1, 0.3, (-1.5, -1.5, 0.0))
     c = 0.375          # exact in binary, so all particles tie exactly
