@@ -41,6 +41,11 @@ N_ITERS = 20
 # (1 subtraction + 1 FMA each), |.| accumulation 1 add; FMA counted as 2.
 FLOP_PER_SAMPLE = 9 * 2 + 3 + 7 * 3 + 1
 GATHER_BYTES_PER_SAMPLE = 8 * 4  # eight f32 nodes
+# Bytes of the cell record one sample reads: the eight corners of its cell,
+# as float (f32 storage) or as stored (the 16- and 8-bit records lanes on
+# points read; with a full view lanes on particles read the 32-byte float
+# record).
+RECORD_BYTES = {"f32": 32, "f16": 16, "bf16": 16, "fp8": 8}
 
 
 def parse():
@@ -71,7 +76,7 @@ def parse():
     ap.add_argument("--ref-particles", type=int, default=192,
                     help="particles per reference-arm step (a bounded slice of one iteration)")
     ap.add_argument("--kernel", default=None,
-                    choices=["fitness", "integrate", "align", "batch", "room64", "precision"],
+                    choices=["fitness", "integrate", "align", "batch", "room64", "precision", "probe"],
                     help="time one kernel on the multiroom volume instead of the frame loop (profiling); "
                          "align: loss + pose and node gradients of 64 320x240 frames against a 256^3 volume, "
                          "and the 10-step polish; batch: 32 sequences of mixed camera and volume size stepped "
@@ -253,6 +258,13 @@ def job_rate(units_per_rank: int, world: int, ms_max: float) -> float:
 
 
 def run_reference(args):
+    """The oracle (plain C, FP64) as the reference arm.  One step is one timed
+    slice of a frame's work: the fitness of --ref-particles particles over all
+    points of frame 1.  A frame is 20 x 3073 particle evaluations plus one
+    fusion, so a step covers a fraction phi of a frame (phi = the slice's time
+    over the frame time that the slice and the timed fusion extrapolate to);
+    value = phi / (seconds per step) frames/s and ms_per_step is the slice's
+    measured time, so steps x ms_per_step is the time the arm really ran."""
     world, rank, _ = world_info()
     if rank != 0:
         return 0
@@ -261,14 +273,21 @@ def run_reference(args):
     fps, desc, cores, times, t_int, npts = oracle_sample(seq, depths, rels, args.compose_mode, args.ref_particles,
                                                          repeats=steps + warm)
     times = times[warm:]
-    t_particle = float(np.mean(times)) / args.ref_particles
+    t_step = float(np.mean(times))
+    t_particle = t_step / args.ref_particles
     t_frame = N_ITERS * (K_PARTICLES + 1) * t_particle + t_int
-    value = 1.0 / t_frame
+    frames_per_step = t_step / t_frame
+    value = frames_per_step / t_step
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "frames/s", "n_gpus": args.gpus,
-        "steps": steps, "warmup": warm, "ms_per_step": 1e3 * t_frame, "higher_is_better": True,
+        "steps": steps, "warmup": warm, "ms_per_step": 1e3 * t_step, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": workload_config(args),
+        "step": {"work": f"fitness of {args.ref_particles} particles (10 deg / 10 cm spread) over all {npts} "
+                         f"points of frame 1", "frames_per_step": frames_per_step,
+                 "frame_ms_extrapolated": 1e3 * t_frame, "fusion_ms": 1e3 * t_int,
+                 "note": "value = frames_per_step / step time; a frame = 20 x 3073 particle evaluations + 1 "
+                         "fusion (fusion timed once, outside the steps)"},
         "cpu_baseline": {"value": value, "unit": "frames/s", "cores": cores, "kind": "oracle",
                          "sample": desc.replace(f"timed {steps + warm}x", f"timed {steps}x (after {warm} warm-up)")},
         "e2e": {"value": value, "unit": "frames/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -437,6 +456,9 @@ def run_ours(args):
     samples_per_launch = samples / max(1, fit_n)
     achieved_tflops = samples_per_launch * FLOP_PER_SAMPLE / (fit_avg_ms / 1e3) / 1e12
     peak_tflops = fp32_peak_tflops()
+    ceilings = gather_ceilings(pf, dev)
+    rec_bytes = RECORD_BYTES[args.tsdf_dtype]
+    achieved_gbs = samples_per_launch * rec_bytes / (fit_avg_ms / 1e3) / 1e9
     line = {
         "metric": METRIC, "value": value, "unit": "frames/s", "n_gpus": world, "steps": K, "warmup": W,
         "ms_per_step": ms_max / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -444,12 +466,20 @@ def run_ours(args):
         "samples_per_s": samples / (ms / 1e3),
         "fitness_samples_per_s": samples / (fit_ms / 1e3) if fit_ms > 0 else None,
         "fitness_vs_plain": vs_plain,
-        "roofline": {"bound": "alu", "kernel": "fitness_kernel<search>", "achieved": achieved_tflops,
-                     "peak": peak_tflops, "unit": "TFLOP/s", "frac": achieved_tflops / peak_tflops,
-                     "traffic": committed_traffic(), "binding_unit": committed_l1_pipe(),
-                     "avg_launch_ms": fit_avg_ms, "launches": fit_n,
-                     "flop_per_sample": FLOP_PER_SAMPLE, "samples_per_launch": samples_per_launch,
-                     "peak_source": "FP32 lanes x clock: 152 SMs x 128 x 2 flop x 2070 MHz (derived)"},
+        "roofline": {"bound": "l2_gather", "kernel": "fitness_kernel<search>", "achieved": achieved_gbs,
+                     "peak": ceilings["l2_gbs"], "unit": "GB/s", "frac": achieved_gbs / ceilings["l2_gbs"],
+                     "traffic": committed_traffic(), "bytes_per_sample": rec_bytes,
+                     "peak_source": "measured in this run: pf_gather_probe mode 0 (L2 -> SM, 1 KiB per warp-load "
+                                    f"at random positions in a {ceilings['mib']} MiB L2-resident buffer, L1 "
+                                    "bypassed), CUDA events",
+                     "scattered_gather_gbs": ceilings["scattered_gbs"],
+                     "frac_of_scattered_gather": achieved_gbs / ceilings["scattered_gbs"],
+                     "hbm_gbs_measured": measured_peak("hbm_gbs"),
+                     "avg_launch_ms": fit_avg_ms, "launches": fit_n, "samples_per_launch": samples_per_launch,
+                     "alu": {"achieved": achieved_tflops, "peak": peak_tflops, "unit": "TFLOP/s",
+                             "frac": achieved_tflops / peak_tflops, "flop_per_sample": FLOP_PER_SAMPLE,
+                             "peak_source": "FP32 lanes x clock: 152 SMs x 128 x 2 flop x 2070 MHz (derived)"},
+                     "binding_unit": committed_l1_pipe()},
         "kernel_ms": {cls: {"total_ms": v[0], "launches": v[1]} for cls, v in kt.items()},
         "gpu_launches": launches,
         "clocks": clock_info,
@@ -467,13 +497,24 @@ def run_ours(args):
     return 0
 
 
-def fitness_source_sha() -> str:
-    """sha256 prefix of the fitness kernel's sources, as recorded beside the
-    committed ncu capture."""
+def fitness_source_sha(sources=None) -> str:
+    """sha256 prefix of the fitness kernel's device code, as recorded beside
+    the committed ncu capture: csrc/track.cu from the fitness section
+    (FIT_THREADS) to the end of fitness_kernel_batch, followed by the value
+    encoding and storage conversions of csrc/pf_internal.cuh (up to its
+    volume and workspace section).  Host-side edits elsewhere in those files
+    leave it unchanged.  `sources` = (track.cu text, pf_internal.cuh text)."""
     import hashlib
+    if sources is None:
+        csrc = os.path.join(ROOT, "paper_2509_24236_gb300", "csrc")
+        sources = tuple(open(os.path.join(csrc, n)).read() for n in ("track.cu", "pf_internal.cuh"))
+    track, internal = sources
+    a = track.index("constexpr int FIT_THREADS")
+    b = track.index("__global__ void track_begin_kernel")
+    c = internal.index("// Volume and workspace")
     h = hashlib.sha256()
-    for name in ("track.cu", "pf_internal.cuh"):
-        h.update(open(os.path.join(ROOT, "paper_2509_24236_gb300", "csrc", name), "rb").read())
+    h.update(track[a:b].encode())
+    h.update(internal[:c].encode())
     return h.hexdigest()[:16]
 
 
@@ -519,6 +560,40 @@ def fp32_peak_tflops() -> float:
     return 152 * 128 * 2 * 2.070e9 / 1e12
 
 
+def measured_peak(key: str):
+    """A figure of the measured MEASURED_PEAKS.json, or None."""
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))).get(key)
+    except (OSError, ValueError):
+        return None
+
+
+def gather_ceilings(pf, dev, mib: int = 48, loads: int = 2048, reps: int = 5) -> dict:
+    """GB/s of the two memory ceilings of the fitness kernel, measured with
+    pf_gather_probe over an L2-resident buffer of `mib` MiB: mode 0 (L2 -> SM,
+    coalesced 1 KiB warp-loads, L1 bypassed) and mode 1 (one 32-byte record
+    per lane at random positions).  CUDA events on the current stream, after
+    one warm-up launch that also brings the buffer into L2."""
+    import torch
+    n_rec = mib * (1 << 20) // 32
+    buf = torch.rand(n_rec * 8, device=dev)
+    threads = pf.pf_gather_probe(buf, n_rec, 0, loads)
+    out = torch.empty(threads, device=dev)
+    res = {"mib": mib, "loads_per_thread": loads, "threads": threads}
+    for mode, key in ((0, "l2_gbs"), (1, "scattered_gbs")):
+        pf.pf_gather_probe(buf, n_rec, mode, loads, out)
+        torch.cuda.synchronize()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(reps):
+            pf.pf_gather_probe(buf, n_rec, mode, loads, out)
+        b.record()
+        torch.cuda.synchronize()
+        res[key] = reps * threads * loads * 32 / (a.elapsed_time(b) / 1e3) / 1e9
+    return res
+
+
 def fitness_vs_plain(pf, vol, depth, intr, pose, dev, reps=5):
     """Samples/s of pf_fitness with 3072 poses around `pose` over one frame's
     points: the encoded (default) kernel against the plain f32 one."""
@@ -552,32 +627,55 @@ def fitness_vs_plain(pf, vol, depth, intr, pose, dev, reps=5):
 
 
 def run_e2e(pf, vol, gt, depths, rels, intr, params, W, K, dev):
+    """The frames end to end through the C ABI from host memory: per frame
+    the depth image and the relative pose go host -> device (pinned), the
+    initial pose P_t^(0) = P_(t-1) P_(t,t-1) is formed by pf_pose_compose,
+    pf_track_frame_async searches and pf_integrate_async fuses, and the pose
+    and the search record come back device -> host before the next frame
+    (wall clock)."""
+    import ctypes
+
     import torch
     vol.reset()
     pinned = [torch.from_numpy(d).pin_memory() for d in depths]
+    rel_host = [torch.from_numpy(np.ascontiguousarray(r.reshape(16))).pin_memory() for r in rels]
+    stats_sz = ctypes.sizeof(pf.pf_track_stats)
+    pose_host = torch.empty(16, dtype=torch.float64).pin_memory()
+    stats_host = torch.empty(stats_sz, dtype=torch.uint8).pin_memory()
     buf = torch.empty_like(pinned[0], device=dev)
-    P = gt[0].copy()
+    rel_dev = torch.empty(16, dtype=torch.float64, device=dev)
+    # the pose of frame f lives in pose_dev[f % 2] (the previous one in the other slot)
+    pose_dev = torch.empty((2, 16), dtype=torch.float64, device=dev)
+    pose_dev[0].copy_(torch.from_numpy(gt[0].reshape(16).copy()))
+    init_dev = torch.empty(16, dtype=torch.float64, device=dev)
+    stats_dev = torch.empty(stats_sz, dtype=torch.uint8, device=dev)
     buf.copy_(pinned[0], non_blocking=True)
-    vol.integrate(buf, intr, P)
+    vol.integrate_async(buf, intr, pose_dev[0])
 
-    def frame(f, P):
+    def frame(f):
+        prev_dev, out_dev = pose_dev[(f - 1) % 2], pose_dev[f % 2]
         buf.copy_(pinned[f], non_blocking=True)
-        P0 = P @ rels[f]
-        status, P, _ = vol.track_frame(buf, intr, params, P0)
-        vol.integrate(buf, intr, P)
-        return P
+        rel_dev.copy_(rel_host[f], non_blocking=True)
+        pf.pf_pose_compose(prev_dev, rel_dev, init_dev)
+        vol.track_frame_async(buf, intr, params, init_dev, out_dev, stats_dev)
+        vol.integrate_async(buf, intr, out_dev)
+        pose_host.copy_(out_dev, non_blocking=True)
+        stats_host.copy_(stats_dev, non_blocking=True)
+        torch.cuda.current_stream().synchronize()   # the host reads the frame's result
 
     for f in range(1, W + 1):
-        P = frame(f, P)
+        frame(f)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for f in range(W + 1, W + K + 1):
-        P = frame(f, P)
+        frame(f)
     torch.cuda.synchronize()
     dt = time.perf_counter() - t0
     h2d = depths[0].nbytes + 16 * 8
-    d2h = 16 * 8 + __import__("ctypes").sizeof(pf.pf_track_stats)
-    return {"value": K / dt, "unit": "frames/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
+    d2h = 16 * 8 + stats_sz
+    return {"value": K / dt, "unit": "frames/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+            "path": "pinned host depth + relative pose -> pf_pose_compose -> pf_track_frame_async -> "
+                    "pf_integrate_async -> pose + search record to host, synchronised per frame"}
 
 
 def run_kernel(args):
@@ -1047,8 +1145,30 @@ def run_precision(args):
     return 0
 
 
+def run_probe(args):
+    """The fitness kernel's memory ceilings (pf_gather_probe) over buffers of
+    growing size: L2-resident ones give the L2 -> SM bandwidth (mode 0) and
+    the scattered-record gather rate (mode 1); the largest spills to HBM."""
+    import torch
+
+    import paper_2509_24236_gb300 as pf
+    from paper_2509_24236_gb300 import build as pfbuild
+    pfbuild.build()
+    pf.load()
+    dev = torch.device("cuda", 0)
+    rows = []
+    for mib in (8, 16, 32, 48, 64, 96, 128, 1024):
+        r = gather_ceilings(pf, dev, mib=mib, loads=2048, reps=max(1, args.reps))
+        rows.append({"mib": mib, "l2_stream_gbs": r["l2_gbs"], "scattered_gbs": r["scattered_gbs"]})
+    print(json.dumps({"kernel": "probe", "threads": r["threads"], "loads_per_thread": 2048, "bytes_per_load": 32,
+                      "rows": rows, "hbm_gbs_measured": measured_peak("hbm_gbs")}))
+    return 0
+
+
 def main():
     args = parse()
+    if args.kernel == "probe":
+        return run_probe(args)
     if args.kernel == "precision":
         return run_precision(args)
     if args.kernel == "room64":

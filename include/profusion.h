@@ -26,6 +26,8 @@
  *     validated on the host before anything is enqueued (PF_ERR_INVALID_ARG,
  *     nothing enqueued).  A CUDA API failure returns PF_ERR_CUDA; faults of
  *     already-enqueued kernels surface at the next call that synchronises.
+ *     Every call that takes a volume also keeps its failing status (any but
+ *     PF_OK and PF_ERR_TRACK_LOST) in the volume: pf_volume_last_error.
  *   - Determinism: identical inputs on the same stream give bit-identical
  *     outputs (fixed reduction orders, no floating-point atomics).
  *   - Concurrency: calls that use the same volume must not overlap on
@@ -164,6 +166,11 @@ PF_API pf_status pf_create_volume(const pf_volume_desc* desc, void* cuda_stream,
 /* Free the volume and its workspace (synchronises the device). NULL is OK. */
 PF_API pf_status pf_destroy_volume(pf_volume* vol);
 
+/* The last failing status (not PF_OK, not PF_ERR_TRACK_LOST) returned by a
+ * call on this volume, PF_OK if none since creation or the last clear;
+ * clear != 0 resets it to PF_OK.  PF_ERR_INVALID_ARG for a NULL volume. */
+PF_API pf_status pf_volume_last_error(pf_volume* vol, int clear);
+
 /* Mark every node unobserved (asynchronous on cuda_stream). */
 PF_API pf_status pf_reset_volume(pf_volume* vol, void* cuda_stream);
 
@@ -228,8 +235,13 @@ PF_API pf_status pf_fitness(const pf_volume* vol, const float* points_dev, int n
  *   k > PF_NOALLOC_MAX_SLOTS is rejected with PF_ERR_INVALID_ARG before
  *   anything is enqueued; smaller k may use fewer point tiles than
  *   pf_fitness, which changes only the float summation order.
- *   The first call on a device looks up the array's device address (set-up,
- *   once per device); make that first call before any stream capture.
+ *   The volume's device must be the current device (else
+ *   PF_ERR_INVALID_ARG: the array used is the current device's).
+ *   The first call on a device is its set-up: it looks up the array's
+ *   device address and loads the code of every fitness kernel the call can
+ *   launch (any storage type, layout or lane mapping), which may allocate;
+ *   make that first call before any stream capture.  Later calls on that
+ *   device allocate nothing (pf_alloc_count does not move).
  *   All calls share the array: calls that overlap on the GPU (other streams,
  *   other host threads) race and must be serialised by the caller. */
 #define PF_NOALLOC_MAX_SLOTS 65536
@@ -337,7 +349,11 @@ PF_API pf_status pf_batch_set_points_per_block(pf_batch* batch, int points_per_b
  *                derivative with respect to the stored (tau-normalised) node
  *                values at fixed cell validity; accumulated in 2^-40 fixed
  *                point, so it is independent of execution order.
- * Geometry and sums are FP64.  The first call allocates library scratch
+ * Arithmetic: each point's grid coordinate is formed in float with
+ * error-free products and sums (no rounding at the scale of the coordinate)
+ * and each sample's residual and gradient in float; the per-frame pose
+ * preparation and the sums across warps and thread blocks are FP64; dL/dV is
+ * accumulated in 2^-40 fixed point (int64).  The first call allocates library scratch
  * (n_frames x 2368 doubles; with grad_tsdf_dev also n_nodes x 8 bytes) kept
  * until the volume is destroyed.  Asynchronous on cuda_stream. */
 PF_API pf_status pf_align_loss(const pf_volume* vol, const float* points_dev, const int* counts_dev, int n_max,
@@ -399,6 +415,30 @@ PF_API const char* pf_status_string(pf_status status);
 
 /* Number of kernels this library has enqueued since it was loaded. */
 PF_API unsigned long long pf_launch_count(void);
+
+/* Number of device allocations (cudaMalloc / cudaMallocAsync) this library
+ * has made since it was loaded. */
+PF_API unsigned long long pf_alloc_count(void);
+
+/* Memory ceilings for the fitness kernel's roofline (the fitness of Sec.
+ * III-B reads one 32-byte cell record per sample, mostly from L2).  Reads
+ * loads_per_thread 32-byte records per thread from buf_dev (n_records
+ * records of 8 floats, n_records a multiple of 32 in [32, 2^31], 32-byte
+ * aligned; size it to fit in L2 and fill it before timing):
+ *   mode 0  each warp reads 32 consecutive records (1 KiB) at a random
+ *           1 KiB-aligned position, bypassing L1: L2 -> SM bandwidth;
+ *   mode 1  each lane reads one record at a random position with the
+ *           fitness kernel's 256-bit read-only load: a fully scattered gather.
+ * Positions follow h <- 1664525 h + 1013904223 (mod 2^32) per warp (mode 0)
+ * or per thread (mode 1), seeded by the murmur3 finaliser of the warp or
+ * thread index; record = floor(h * n / 2^32) (mode 0: block * 32 + lane).
+ * out_dev gets one float per thread: the sum of the values it loaded (each
+ * record's eight values as ((v0+v1)+(v2+v3))+((v4+v5)+(v6+v7)), added in
+ * load order).  *threads_out receives the thread count (out_dev NULL:
+ * only that, nothing launched).  Bytes read = threads x loads x 32; time it
+ * with events on cuda_stream.  Launches one kernel; no synchronisation. */
+PF_API pf_status pf_gather_probe(const float* buf_dev, long long n_records, int mode, int loads_per_thread,
+                                 float* out_dev, long long* threads_out, void* cuda_stream);
 
 /* When enabled, every launch of the named kernel class ("fitness": the
  * search and pf_fitness launches; "fitness1": the single-pose evaluation of

@@ -66,7 +66,8 @@ EXPORTS = ["pf_create_volume", "pf_destroy_volume", "pf_reset_volume", "pf_volum
            "pf_track_reserve", "pf_raycast", "pf_set_fitness_variant", "pf_status_string", "pf_launch_count",
            "pf_set_kernel_timing", "pf_kernel_timing", "pf_align_loss", "pf_polish",
            "pf_batch_create", "pf_batch_destroy", "pf_batch_buffers", "pf_batch_fuse", "pf_batch_step",
-           "pf_batch_autotune", "pf_batch_set_points_per_block", "pf_volume_info"]
+           "pf_batch_autotune", "pf_batch_set_points_per_block", "pf_volume_info", "pf_alloc_count", "pf_volume_last_error",
+           "pf_gather_probe"]
 
 _lib = None
 
@@ -110,6 +111,9 @@ def load(path: str = LIB_PATH):
         "pf_volume_info": (st, [vp, C.POINTER(C.c_ulonglong), C.POINTER(C.c_int)]),
         "pf_status_string": (C.c_char_p, [st]),
         "pf_launch_count": (C.c_ulonglong, []),
+        "pf_alloc_count": (C.c_ulonglong, []),
+        "pf_volume_last_error": (st, [vp, C.c_int]),
+        "pf_gather_probe": (st, [vp, C.c_longlong, C.c_int, C.c_int, vp, C.POINTER(C.c_longlong), vp]),
         "pf_set_kernel_timing": (st, [C.c_int]),
         "pf_kernel_timing": (st, [C.c_char_p, dp, C.POINTER(C.c_longlong)]),
         "pf_align_loss": (st, [vp, vp, vp, C.c_int, C.c_int, vp, vp, vp, vp, vp, vp, vp, vp]),
@@ -316,6 +320,27 @@ def pf_volume_info(vol):
 
 def pf_launch_count() -> int:
     return int(load().pf_launch_count())
+
+
+def pf_volume_last_error(vol, clear: bool = False) -> int:
+    """The last failing status of a call on the volume (PF_OK if none)."""
+    return int(load().pf_volume_last_error(vol, 1 if clear else 0))
+
+
+def pf_alloc_count() -> int:
+    """Device allocations the library has made since it was loaded."""
+    return int(load().pf_alloc_count())
+
+
+def pf_gather_probe(buf, n_records: int, mode: int, loads_per_thread: int, out=None, stream=None) -> int:
+    """Launch the memory-ceiling probe (mode 0: L2 -> SM stream, 1: scattered
+    32-byte records) over `buf` (n_records x 8 float32, on the device);
+    returns the thread count (out None: only that, nothing launched)."""
+    import torch
+    n = C.c_longlong(0)
+    _check(load().pf_gather_probe(_dptr(buf, torch.float32), int(n_records), int(mode), int(loads_per_thread),
+                                  _dptr(out, torch.float32), C.byref(n), _stream(stream)), "pf_gather_probe")
+    return int(n.value)
 
 
 def pf_set_kernel_timing(enable: bool) -> int:

@@ -770,7 +770,7 @@ void align_release(const pf_volume* v)
 
 extern "C" {
 
-pf_status pf_align_loss(const pf_volume* v, const float* points_dev, const int* counts_dev, int n_max, int n_frames,
+static pf_status pf_align_loss_impl(const pf_volume* v, const float* points_dev, const int* counts_dev, int n_max, int n_frames,
                         const double* poses_dev, const double* xi_dev, const double* dloss_dev, double* loss_dev,
                         int* count_dev, double* grad_xi_dev, float* grad_tsdf_dev, void* stream)
 {
@@ -785,17 +785,17 @@ pf_status pf_align_loss(const pf_volume* v, const float* points_dev, const int* 
         cudaFree(sc.part);
         sc.part = nullptr;
         sc.part_cap = 0;
-        PF_CUDA(cudaMalloc(&sc.part, need * sizeof(double)));
+        PF_CUDA(pf::dev_malloc(&sc.part, need * sizeof(double)));
         sc.part_cap = need;
     }
     if (sc.frame_cap < n_frames) {
         cudaFree(sc.frame_pose);
         sc.frame_pose = nullptr;
         sc.frame_cap = 0;
-        PF_CUDA(cudaMalloc(&sc.frame_pose, (size_t)n_frames * sizeof(FramePose)));
+        PF_CUDA(pf::dev_malloc(&sc.frame_pose, (size_t)n_frames * sizeof(FramePose)));
         sc.frame_cap = n_frames;
     }
-    if (grad_tsdf_dev && !sc.acc) PF_CUDA(cudaMalloc(&sc.acc, v->n_nodes * sizeof(long long)));
+    if (grad_tsdf_dev && !sc.acc) PF_CUDA(pf::dev_malloc(&sc.acc, v->n_nodes * sizeof(long long)));
     if (grad_tsdf_dev) PF_CUDA(cudaMemsetAsync(sc.acc, 0, v->n_nodes * sizeof(long long), s));
     AlignArgs a;
     a.tsdf = v->tsdf;
@@ -826,7 +826,7 @@ pf_status pf_align_loss(const pf_volume* v, const float* points_dev, const int* 
     return PF_OK;
 }
 
-pf_status pf_polish(const pf_volume* v, const float* points_dev, const int* n_dev, int n_max, double* pose_dev,
+static pf_status pf_polish_impl(const pf_volume* v, const float* points_dev, const int* n_dev, int n_max, double* pose_dev,
                     int steps, double* trace_dev, int* accepted_dev, void* stream)
 {
     if (!v || !pose_dev || n_max < 0 || steps < 0 || steps > 1000) return PF_ERR_INVALID_ARG;
@@ -834,9 +834,9 @@ pf_status pf_polish(const pf_volume* v, const float* points_dev, const int* n_de
     if (((uintptr_t)points_dev & 15) != 0) return PF_ERR_INVALID_ARG;
     cudaStream_t s = (cudaStream_t)stream;
     AlignScratch& sc = scratch_of(v);
-    if (!sc.gn_part) PF_CUDA(cudaMalloc(&sc.gn_part, (size_t)AL_TILES * GN_VALS * sizeof(double)));
-    if (!sc.gn_state) PF_CUDA(cudaMalloc(&sc.gn_state, sizeof(GnState)));
-    if (!sc.gn_pose) PF_CUDA(cudaMalloc(&sc.gn_pose, sizeof(PoseF)));
+    if (!sc.gn_part) PF_CUDA(pf::dev_malloc(&sc.gn_part, (size_t)AL_TILES * GN_VALS * sizeof(double)));
+    if (!sc.gn_state) PF_CUDA(pf::dev_malloc(&sc.gn_state, sizeof(GnState)));
+    if (!sc.gn_pose) PF_CUDA(pf::dev_malloc(&sc.gn_pose, sizeof(PoseF)));
     PoseF* pc = static_cast<PoseF*>(sc.gn_pose);
     GnState* st = reinterpret_cast<GnState*>(sc.gn_state);
 
@@ -864,6 +864,22 @@ pf_status pf_polish(const pf_volume* v, const float* points_dev, const int* n_de
         PF_LAUNCHED();
     }
     return PF_OK;
+}
+
+}  // extern "C"
+
+// Every entry point that takes a volume keeps its last failing status
+// there (pf_volume_last_error).
+extern "C" {
+
+pf_status pf_align_loss(const pf_volume* v, const float* points_dev, const int* counts_dev, int n_max, int n_frames, const double* poses_dev, const double* xi_dev, const double* dloss_dev, double* loss_dev, int* count_dev, double* grad_xi_dev, float* grad_tsdf_dev, void* stream)
+{
+    return pf::keep_status(v, pf_align_loss_impl(v, points_dev, counts_dev, n_max, n_frames, poses_dev, xi_dev, dloss_dev, loss_dev, count_dev, grad_xi_dev, grad_tsdf_dev, stream));
+}
+
+pf_status pf_polish(const pf_volume* v, const float* points_dev, const int* n_dev, int n_max, double* pose_dev, int steps, double* trace_dev, int* accepted_dev, void* stream)
+{
+    return pf::keep_status(v, pf_polish_impl(v, points_dev, n_dev, n_max, pose_dev, steps, trace_dev, accepted_dev, stream));
 }
 
 }  // extern "C"

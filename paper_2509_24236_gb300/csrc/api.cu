@@ -9,6 +9,7 @@
 namespace pf {
 
 std::atomic<unsigned long long> g_launches{0};
+std::atomic<unsigned long long> g_allocs{0};
 
 namespace {
 
@@ -107,6 +108,8 @@ const char* pf_status_string(pf_status s)
 }
 
 unsigned long long pf_launch_count(void) { return pf::g_launches.load(); }
+
+unsigned long long pf_alloc_count(void) { return pf::g_allocs.load(); }
 
 pf_status pf_set_kernel_timing(int enable)
 {

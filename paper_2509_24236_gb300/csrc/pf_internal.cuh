@@ -143,6 +143,7 @@ struct pf_volume {
     int stamp = 0;             // fusions so far
     int tiles[3] = {0, 0, 0};
     int fitness_variant = 0;
+    pf_status last_status = PF_OK;  // last failing status of a call on this volume
     pf_workspace ws;
 };
 
@@ -152,8 +153,25 @@ struct pf_volume {
 namespace pf {
 
 extern std::atomic<unsigned long long> g_launches;
+extern std::atomic<unsigned long long> g_allocs;
 
 inline void count_launch(unsigned n = 1) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+
+// Every device allocation the library makes goes through these two, so that
+// pf_alloc_count can tell a caller whether a call allocated.
+template <typename T>
+inline cudaError_t dev_malloc(T** p, size_t bytes)
+{
+    g_allocs.fetch_add(1, std::memory_order_relaxed);
+    return cudaMalloc(reinterpret_cast<void**>(p), bytes);
+}
+
+template <typename T>
+inline cudaError_t dev_malloc_async(T** p, size_t bytes, cudaStream_t s)
+{
+    g_allocs.fetch_add(1, std::memory_order_relaxed);
+    return cudaMallocAsync(reinterpret_cast<void**>(p), bytes, s);
+}
 
 enum KernelClass { KC_FITNESS = 0, KC_FITNESS1, KC_INTEGRATE, KC_REFRESH, KC_BACKPROJECT, KC_RAYCAST, KC_COUNT };
 
@@ -163,6 +181,14 @@ void timing_end(KernelClass kc, cudaStream_t s);
 
 pf_status check_intrinsics(const pf_intrinsics* intr);
 pf_status workspace_reserve(pf_volume* vol, int max_pixels, int k_max);
+
+// Records a failing status (anything but PF_OK and PF_ERR_TRACK_LOST, which
+// describes the frame rather than the call) in the volume it concerns.
+inline pf_status keep_status(const pf_volume* v, pf_status s)
+{
+    if (v && s != PF_OK && s != PF_ERR_TRACK_LOST) const_cast<pf_volume*>(v)->last_status = s;
+    return s;
+}
 
 inline pf_status cuda_status(cudaError_t e)
 {

@@ -114,7 +114,7 @@ __global__ void raycast_kernel(RayArgs a)
 
 }  // namespace
 
-extern "C" pf_status pf_raycast(const pf_volume* v, const pf_intrinsics* intr, const double P[16],
+static pf_status pf_raycast_impl(const pf_volume* v, const pf_intrinsics* intr, const double P[16],
                                 float* depth_out, float* normal_out, void* stream)
 {
     if (!v || !P || !depth_out) return PF_ERR_INVALID_ARG;
@@ -157,3 +157,14 @@ extern "C" pf_status pf_raycast(const pf_volume* v, const pf_intrinsics* intr, c
     PF_LAUNCHED();
     return PF_OK;
 }
+
+// Every entry point that takes a volume keeps its last failing status
+// there (pf_volume_last_error).
+extern "C" {
+
+pf_status pf_raycast(const pf_volume* v, const pf_intrinsics* intr, const double P[16], float* depth_out, float* normal_out, void* stream)
+{
+    return pf::keep_status(v, pf_raycast_impl(v, intr, P, depth_out, normal_out, stream));
+}
+
+}  // extern "C"

@@ -1467,7 +1467,7 @@ pf_status grow_partials(pf_volume* v, size_t need)
     if ((size_t)w.part_cap >= need && w.counter) return PF_OK;
     PF_CUDA(cudaDeviceSynchronize());
     if (!w.counter) {
-        PF_CUDA(cudaMalloc(&w.counter, sizeof(unsigned int)));
+        PF_CUDA(pf::dev_malloc(&w.counter, sizeof(unsigned int)));
         PF_CUDA(cudaMemset(w.counter, 0, sizeof(unsigned int)));
     }
     if ((size_t)w.part_cap < need) {
@@ -1476,8 +1476,8 @@ pf_status grow_partials(pf_volume* v, size_t need)
         w.part_S = nullptr;
         w.part_C = nullptr;
         w.part_cap = 0;
-        PF_CUDA(cudaMalloc(&w.part_S, need * sizeof(float)));
-        PF_CUDA(cudaMalloc(&w.part_C, need * sizeof(int)));
+        PF_CUDA(pf::dev_malloc(&w.part_S, need * sizeof(float)));
+        PF_CUDA(pf::dev_malloc(&w.part_C, need * sizeof(int)));
         w.part_cap = (int)need;
     }
     return PF_OK;
@@ -1527,18 +1527,18 @@ pf_status workspace_reserve(pf_volume* v, int max_pixels, int k_max)
         w.points = nullptr;
         w.block_counts = nullptr;
         w.pix_cap = 0;
-        PF_CUDA(cudaMalloc(&w.points, sizeof(float4) * (size_t)max_pixels));
+        PF_CUDA(pf::dev_malloc(&w.points, sizeof(float4) * (size_t)max_pixels));
         // one count per back-projection block: an image of max_pixels pixels has
         // at most max_pixels tiles (thin images leave tiles partly empty)
-        PF_CUDA(cudaMalloc(&w.block_counts, sizeof(int) * ((size_t)max_pixels / BP_CHUNK_TILES + 2)));
+        PF_CUDA(pf::dev_malloc(&w.block_counts, sizeof(int) * ((size_t)max_pixels / BP_CHUNK_TILES + 2)));
         w.pix_cap = max_pixels;
     }
     if (!w.state) {
-        PF_CUDA(cudaMalloc(&w.state, sizeof(SearchState)));
-        PF_CUDA(cudaMalloc(&w.n_points, sizeof(int)));
-        PF_CUDA(cudaMalloc(&w.pose_in, 16 * sizeof(double)));
-        PF_CUDA(cudaMalloc(&w.pose_out, 16 * sizeof(double)));
-        PF_CUDA(cudaMalloc(&w.stats, sizeof(pf_track_stats)));
+        PF_CUDA(pf::dev_malloc(&w.state, sizeof(SearchState)));
+        PF_CUDA(pf::dev_malloc(&w.n_points, sizeof(int)));
+        PF_CUDA(pf::dev_malloc(&w.pose_in, 16 * sizeof(double)));
+        PF_CUDA(pf::dev_malloc(&w.pose_out, 16 * sizeof(double)));
+        PF_CUDA(pf::dev_malloc(&w.stats, sizeof(pf_track_stats)));
         PF_CUDA(cudaMemset(w.stats, 0, sizeof(pf_track_stats)));
     }
     w.k_cap = std::max(w.k_cap, k_max);
@@ -1559,14 +1559,14 @@ pf_status pf_backproject(const float* depth_dev, const pf_intrinsics* intr, floa
     if (capacity < npix) return PF_ERR_INVALID_ARG;
     int* counts = nullptr;
     const int blocks = bp_blocks(intr->width, intr->height);
-    PF_CUDA(cudaMallocAsync(&counts, sizeof(int) * blocks, (cudaStream_t)stream));
+    PF_CUDA(pf::dev_malloc_async(&counts, sizeof(int) * blocks, (cudaStream_t)stream));
     st = enqueue_backproject(depth_dev, intr, reinterpret_cast<float4*>(points_dev), counts, n_dev,
                              (cudaStream_t)stream);
     cudaFreeAsync(counts, (cudaStream_t)stream);
     return st;
 }
 
-pf_status pf_fitness(const pf_volume* cv, const float* points_dev, int n, const float* poses_dev, int k,
+static pf_status pf_fitness_impl(const pf_volume* cv, const float* points_dev, int n, const float* poses_dev, int k,
                      float* fitness_dev, int* count_dev, void* stream)
 {
     pf_volume* v = const_cast<pf_volume*>(cv);
@@ -1599,12 +1599,12 @@ pf_status pf_fitness(const pf_volume* cv, const float* points_dev, int n, const 
     return PF_OK;
 }
 
-pf_status pf_track_reserve(pf_volume* v, int max_pixels, int k_max)
+static pf_status pf_track_reserve_impl(pf_volume* v, int max_pixels, int k_max)
 {
     return pf::workspace_reserve(v, max_pixels, k_max);
 }
 
-pf_status pf_track_frame_async(pf_volume* v, const float* depth_dev, const pf_intrinsics* intr,
+static pf_status pf_track_frame_async_impl(pf_volume* v, const float* depth_dev, const pf_intrinsics* intr,
                                const pf_track_params* p, const double* init_pose_dev, double* out_pose_dev,
                                pf_track_stats* stats_dev, void* stream)
 {
@@ -1671,7 +1671,7 @@ pf_status pf_track_frame_async(pf_volume* v, const float* depth_dev, const pf_in
     return PF_OK;
 }
 
-pf_status pf_track_frame(pf_volume* v, const float* depth_dev, const pf_intrinsics* intr, const pf_track_params* p,
+static pf_status pf_track_frame_impl(pf_volume* v, const float* depth_dev, const pf_intrinsics* intr, const pf_track_params* p,
                          const double init_pose[16], double out_pose[16], pf_track_stats* stats_host,
                          void* stream)
 {
@@ -1702,19 +1702,6 @@ pf_status pf_track_frame(pf_volume* v, const float* depth_dev, const pf_intrinsi
 
 }  // extern "C"
 
-// ---------------------------------------------------------------------------
-// Fitness without any device allocation.
-//
-// pf_fitness keeps its per-tile partial sums in the volume's workspace and
-// grows it with cudaMalloc when a call needs more.  Callers that must not
-// allocate device memory once they are running -- for instance a process
-// whose device memory is owned by another allocator, or a real-time loop
-// that cannot afford the device-wide synchronisation a cudaMalloc implies --
-// use pf_fitness_noalloc instead: the same kernel, with its scratch (the
-// partial sums and the ticket counter of the last-block reduction) in the
-// fixed array below, which every device that loads the library holds until
-// the process exits.
-// ---------------------------------------------------------------------------
 // ---------------------------------------------------------------------------
 // Batches: many independent sequences stepped together
 // ---------------------------------------------------------------------------
@@ -1865,8 +1852,8 @@ pf_status batch_tables(pf_batch* b, bool tune)
         }
     }
     if (!b->d_args) {
-        PF_CUDA(cudaMalloc(&b->d_args, args.size() * sizeof(FitArgs)));
-        PF_CUDA(cudaMalloc(&b->d_first, first.size() * sizeof(int)));
+        PF_CUDA(pf::dev_malloc(&b->d_args, args.size() * sizeof(FitArgs)));
+        PF_CUDA(pf::dev_malloc(&b->d_first, first.size() * sizeof(int)));
     }
     PF_CUDA(cudaMemcpy(b->d_args, args.data(), args.size() * sizeof(FitArgs), cudaMemcpyHostToDevice));
     PF_CUDA(cudaMemcpy(b->d_first, first.data(), first.size() * sizeof(int), cudaMemcpyHostToDevice));
@@ -1991,14 +1978,14 @@ pf_status pf_batch_create(int n, pf_volume* const* vols, const pf_intrinsics* in
                                    std::max(params[i].k_max, w.k_cap));
     }
     if (st != PF_OK) return fail(st);
-    cudaError_t e = cudaMalloc(&b->depth, depth_total * sizeof(float));
+    cudaError_t e = pf::dev_malloc(&b->depth, depth_total * sizeof(float));
     if (e == cudaSuccess) e = cudaMemset(b->depth, 0, depth_total * sizeof(float));
-    if (e == cudaSuccess) e = cudaMalloc(&b->poses, (size_t)n * 64 * sizeof(double));
+    if (e == cudaSuccess) e = pf::dev_malloc(&b->poses, (size_t)n * 64 * sizeof(double));
     if (e == cudaSuccess) e = cudaMemset(b->poses, 0, (size_t)n * 64 * sizeof(double));
-    if (e == cudaSuccess) e = cudaMalloc(&b->stats, (size_t)n * sizeof(pf_track_stats));
+    if (e == cudaSuccess) e = pf::dev_malloc(&b->stats, (size_t)n * sizeof(pf_track_stats));
     if (e == cudaSuccess) e = cudaMemset(b->stats, 0, (size_t)n * sizeof(pf_track_stats));
-    if (e == cudaSuccess) e = cudaMalloc(&b->tune_state, (size_t)n * sizeof(SearchState));
-    if (e == cudaSuccess) e = cudaMalloc(&b->tune_stats, (size_t)n * sizeof(pf_track_stats));
+    if (e == cudaSuccess) e = pf::dev_malloc(&b->tune_state, (size_t)n * sizeof(SearchState));
+    if (e == cudaSuccess) e = pf::dev_malloc(&b->tune_stats, (size_t)n * sizeof(pf_track_stats));
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
     if (e != cudaSuccess) return fail(pf::cuda_status(e));
     // identity poses
@@ -2153,6 +2140,19 @@ pf_status pf_batch_autotune(pf_batch* b, void* stream, int* chosen)
 
 }  // extern "C"
 
+// ---------------------------------------------------------------------------
+// Fitness without any device allocation.
+//
+// pf_fitness keeps its per-tile partial sums in the volume's workspace and
+// grows it with cudaMalloc when a call needs more.  Callers that must not
+// allocate device memory once they are running -- for instance a process
+// whose device memory is owned by another allocator, or a real-time loop
+// that cannot afford the device-wide synchronisation a cudaMalloc implies --
+// use pf_fitness_noalloc instead: the same kernel, with its scratch (the
+// partial sums and the ticket counter of the last-block reduction) in the
+// fixed array below, which every device that loads the library holds until
+// the process exits.
+// ---------------------------------------------------------------------------
 namespace {
 
 struct NoAllocScratch {
@@ -2168,19 +2168,49 @@ constexpr int kMaxDevices = 64;
 std::mutex g_noalloc_mu;
 NoAllocScratch* g_noalloc_addr[kMaxDevices] = {};
 
-// Device address of the scratch array on the current device, looked up once
-// per device (the first call on a device does this set-up).
-pf_status noalloc_scratch(NoAllocScratch** out)
+// Loads the code of every fitness kernel pf_fitness_noalloc can launch (each
+// layout and storage type) on the current device.  With lazy module loading,
+// a kernel's code is loaded -- into newly allocated device memory -- on its
+// first launch; doing it here, in the set-up, keeps later calls free of
+// allocations whatever volume they are given.
+template <typename TS>
+cudaError_t preload_fitness_storage()
+{
+    cudaFuncAttributes fa;
+    cudaError_t e = cudaFuncGetAttributes(&fa, fitness_kernel<SRC_POSES, 0, TS>);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, fitness_kernel<SRC_POSES, 2, TS>);
+    return e;
+}
+
+cudaError_t preload_fitness_kernels()
+{
+    cudaFuncAttributes fa;
+    cudaError_t e = cudaFuncGetAttributes(&fa, fitness_kernel<SRC_POSES, 1, float>);
+    if (e == cudaSuccess) e = preload_fitness_storage<float>();
+    if (e == cudaSuccess) e = preload_fitness_storage<__half>();
+    if (e == cudaSuccess) e = preload_fitness_storage<__nv_bfloat16>();
+    if (e == cudaSuccess) e = preload_fitness_storage<__nv_fp8_e4m3>();
+    return e;
+}
+
+// Device address of the scratch array on the current device, which must be
+// `device`.  The first call on a device is the set-up: it looks the address
+// up and loads the kernels (both may allocate); later calls only read the
+// cached address.
+pf_status noalloc_scratch(int device, NoAllocScratch** out)
 {
     int dev = 0;
     PF_CUDA(cudaGetDevice(&dev));
+    if (dev != device) return PF_ERR_INVALID_ARG;  // the array and the volume would be on different devices
     if (dev < 0 || dev >= kMaxDevices) return PF_ERR_UNSUPPORTED;
     std::lock_guard<std::mutex> lock(g_noalloc_mu);
     if (!g_noalloc_addr[dev]) {
         void* p = nullptr;
-        const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
         if (e != cudaSuccess) return pf::cuda_status(e);
         if (!p) return PF_ERR_CUDA;
+        e = preload_fitness_kernels();
+        if (e != cudaSuccess) return pf::cuda_status(e);
         g_noalloc_addr[dev] = static_cast<NoAllocScratch*>(p);
     }
     *out = g_noalloc_addr[dev];
@@ -2189,14 +2219,14 @@ pf_status noalloc_scratch(NoAllocScratch** out)
 
 }  // namespace
 
-extern "C" pf_status pf_fitness_noalloc(const pf_volume* v, const float* points_dev, int n, const float* poses_dev,
+static pf_status pf_fitness_noalloc_impl(const pf_volume* v, const float* points_dev, int n, const float* poses_dev,
                                         int k, float* fitness_dev, int* count_dev, void* stream)
 {
     if (!v || !poses_dev || !fitness_dev || !count_dev) return PF_ERR_INVALID_ARG;
     if (n < 0 || k < 1 || (n > 0 && !points_dev)) return PF_ERR_INVALID_ARG;
     if (k > PF_NOALLOC_MAX_SLOTS) return PF_ERR_INVALID_ARG;  // more poses than the scratch holds
     NoAllocScratch* sc = nullptr;
-    pf_status st = noalloc_scratch(&sc);
+    pf_status st = noalloc_scratch(v->device, &sc);
     if (st != PF_OK) return st;
     const int chunks = (k + KC - 1) / KC;
     // as many point tiles as pf_fitness would use, within the fixed scratch
@@ -2223,3 +2253,34 @@ extern "C" pf_status pf_fitness_noalloc(const pf_volume* v, const float* points_
     PF_LAUNCHED();
     return PF_OK;
 }
+
+// Every entry point that takes a volume keeps its last failing status
+// there (pf_volume_last_error).
+extern "C" {
+
+pf_status pf_fitness(const pf_volume* cv, const float* points_dev, int n, const float* poses_dev, int k, float* fitness_dev, int* count_dev, void* stream)
+{
+    return pf::keep_status(cv, pf_fitness_impl(cv, points_dev, n, poses_dev, k, fitness_dev, count_dev, stream));
+}
+
+pf_status pf_track_reserve(pf_volume* v, int max_pixels, int k_max)
+{
+    return pf::keep_status(v, pf_track_reserve_impl(v, max_pixels, k_max));
+}
+
+pf_status pf_track_frame_async(pf_volume* v, const float* depth_dev, const pf_intrinsics* intr, const pf_track_params* p, const double* init_pose_dev, double* out_pose_dev, pf_track_stats* stats_dev, void* stream)
+{
+    return pf::keep_status(v, pf_track_frame_async_impl(v, depth_dev, intr, p, init_pose_dev, out_pose_dev, stats_dev, stream));
+}
+
+pf_status pf_track_frame(pf_volume* v, const float* depth_dev, const pf_intrinsics* intr, const pf_track_params* p, const double init_pose[16], double out_pose[16], pf_track_stats* stats_host, void* stream)
+{
+    return pf::keep_status(v, pf_track_frame_impl(v, depth_dev, intr, p, init_pose, out_pose, stats_host, stream));
+}
+
+pf_status pf_fitness_noalloc(const pf_volume* v, const float* points_dev, int n, const float* poses_dev, int k, float* fitness_dev, int* count_dev, void* stream)
+{
+    return pf::keep_status(v, pf_fitness_noalloc_impl(v, points_dev, n, poses_dev, k, fitness_dev, count_dev, stream));
+}
+
+}  // extern "C"

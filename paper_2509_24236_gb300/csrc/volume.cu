@@ -370,12 +370,12 @@ pf_status pf_create_volume(const pf_volume_desc* desc, void* stream, pf_volume**
     if (mode == 2 && !bytes32) mode = 1;
     const bool view = mode >= 1;
     const bool wide = mode == 1;
-    if (e == cudaSuccess) e = cudaMalloc(&v->tsdf, v->n_nodes * ts);
-    if (e == cudaSuccess) e = cudaMalloc(&v->weight, v->n_nodes * ws);
-    if (e == cudaSuccess && view) e = cudaMalloc(&v->cells, view_bytes);
-    if (e == cudaSuccess && wide && bytes32) e = cudaMalloc(&v->cells32, bytes32);
+    if (e == cudaSuccess) e = pf::dev_malloc(&v->tsdf, v->n_nodes * ts);
+    if (e == cudaSuccess) e = pf::dev_malloc(&v->weight, v->n_nodes * ws);
+    if (e == cudaSuccess && view) e = pf::dev_malloc(&v->cells, view_bytes);
+    if (e == cudaSuccess && wide && bytes32) e = pf::dev_malloc(&v->cells32, bytes32);
     if (e == cudaSuccess && view)
-        e = cudaMalloc(&v->tile_stamp, sizeof(int) * ((size_t)v->tiles[0] * v->tiles[1] * v->tiles[2] + 1));
+        e = pf::dev_malloc(&v->tile_stamp, sizeof(int) * ((size_t)v->tiles[0] * v->tiles[1] * v->tiles[2] + 1));
     if (e == cudaSuccess && view)
         e = cudaMemset(v->tile_stamp, 0, sizeof(int) * ((size_t)v->tiles[0] * v->tiles[1] * v->tiles[2] + 1));
     if (e != cudaSuccess) {
@@ -422,13 +422,13 @@ pf_status pf_destroy_volume(pf_volume* v)
     return PF_OK;
 }
 
-pf_status pf_reset_volume(pf_volume* v, void* stream)
+static pf_status pf_reset_volume_impl(pf_volume* v, void* stream)
 {
     if (!v) return PF_ERR_INVALID_ARG;
     return enqueue_reset(v, (cudaStream_t)stream);
 }
 
-pf_status pf_set_fitness_variant(pf_volume* v, int variant)
+static pf_status pf_set_fitness_variant_impl(pf_volume* v, int variant)
 {
     if (!v || variant < 0 || variant > 11 || (variant & 3) == 3 && !v->cells) return PF_ERR_INVALID_ARG;
     // the plain baseline exists for float tsdf and float weights only
@@ -479,7 +479,7 @@ float load_host(pf_dtype dt, const unsigned char* src)
 
 extern "C" {
 
-pf_status pf_volume_upload(pf_volume* v, const float* tsdf_host, const float* weight_host)
+static pf_status pf_volume_upload_impl(pf_volume* v, const float* tsdf_host, const float* weight_host)
 {
     if (!v || !tsdf_host || !weight_host) return PF_ERR_INVALID_ARG;
     const size_t n = v->n_nodes;
@@ -505,7 +505,7 @@ pf_status pf_volume_upload(pf_volume* v, const float* tsdf_host, const float* we
     return PF_OK;
 }
 
-pf_status pf_volume_download(const pf_volume* v, float* tsdf_host, float* weight_host)
+static pf_status pf_volume_download_impl(const pf_volume* v, float* tsdf_host, float* weight_host)
 {
     if (!v || !tsdf_host || !weight_host) return PF_ERR_INVALID_ARG;
     const size_t n = v->n_nodes;
@@ -611,14 +611,14 @@ __global__ void compose_kernel(const double* A, const double* B, double* out)
 
 extern "C" {
 
-pf_status pf_integrate(pf_volume* v, const float* depth_dev, const pf_intrinsics* intr, const double P[16],
+static pf_status pf_integrate_impl(pf_volume* v, const float* depth_dev, const pf_intrinsics* intr, const double P[16],
                        void* stream)
 {
     if (!P || !finite_pose(P)) return PF_ERR_INVALID_ARG;
     return integrate_impl(v, depth_dev, intr, P, nullptr, (cudaStream_t)stream);
 }
 
-pf_status pf_integrate_async(pf_volume* v, const float* depth_dev, const pf_intrinsics* intr,
+static pf_status pf_integrate_async_impl(pf_volume* v, const float* depth_dev, const pf_intrinsics* intr,
                              const double* P_dev, void* stream)
 {
     if (!P_dev) return PF_ERR_INVALID_ARG;
@@ -632,6 +632,50 @@ pf_status pf_pose_compose(const double* a_dev, const double* b_dev, double* out_
     pf::count_launch();
     PF_LAUNCHED();
     return PF_OK;
+}
+
+}  // extern "C"
+
+// Every entry point that takes a volume keeps its last failing status
+// there (pf_volume_last_error).
+extern "C" {
+
+pf_status pf_volume_last_error(pf_volume* v, int clear)
+{
+    if (!v) return PF_ERR_INVALID_ARG;
+    const pf_status s = v->last_status;
+    if (clear) v->last_status = PF_OK;
+    return s;
+}
+
+pf_status pf_reset_volume(pf_volume* v, void* stream)
+{
+    return pf::keep_status(v, pf_reset_volume_impl(v, stream));
+}
+
+pf_status pf_set_fitness_variant(pf_volume* v, int variant)
+{
+    return pf::keep_status(v, pf_set_fitness_variant_impl(v, variant));
+}
+
+pf_status pf_volume_upload(pf_volume* v, const float* tsdf_host, const float* weight_host)
+{
+    return pf::keep_status(v, pf_volume_upload_impl(v, tsdf_host, weight_host));
+}
+
+pf_status pf_volume_download(const pf_volume* v, float* tsdf_host, float* weight_host)
+{
+    return pf::keep_status(v, pf_volume_download_impl(v, tsdf_host, weight_host));
+}
+
+pf_status pf_integrate(pf_volume* v, const float* depth_dev, const pf_intrinsics* intr, const double P[16], void* stream)
+{
+    return pf::keep_status(v, pf_integrate_impl(v, depth_dev, intr, P, stream));
+}
+
+pf_status pf_integrate_async(pf_volume* v, const float* depth_dev, const pf_intrinsics* intr, const double* P_dev, void* stream)
+{
+    return pf::keep_status(v, pf_integrate_async_impl(v, depth_dev, intr, P_dev, stream));
 }
 
 }  // extern "C"

@@ -118,3 +118,17 @@ def test_binding_refuses_to_run_without_the_library(tmp_path):
             pf.load(str(tmp_path / "missing.so"))
         finally:
             pf._lib = pf._lib_backup
+
+
+def test_instrumentation_validation_without_a_gpu(lib):
+    import paper_2509_24236_gb300 as pf
+    assert lib.pf_volume_last_error(None, 0) == pf.PF_ERR_INVALID_ARG
+    n = C.c_longlong(0)
+    buf = C.c_void_p(1 << 20)   # never dereferenced: every case below fails host-side checks first
+    assert lib.pf_gather_probe(buf, 64, 0, 1, None, None, None) == pf.PF_ERR_INVALID_ARG      # no output count
+    assert lib.pf_gather_probe(buf, 64, 2, 1, None, C.byref(n), None) == pf.PF_ERR_INVALID_ARG  # mode
+    assert lib.pf_gather_probe(buf, 48, 0, 1, None, C.byref(n), None) == pf.PF_ERR_INVALID_ARG  # not a multiple of 32
+    assert lib.pf_gather_probe(buf, 64, 0, 0, None, C.byref(n), None) == pf.PF_ERR_INVALID_ARG  # no loads
+    assert lib.pf_gather_probe(C.c_void_p((1 << 20) + 16), 64, 0, 1, None, C.byref(n), None) == \
+        pf.PF_ERR_INVALID_ARG                                                                   # misaligned
+    assert isinstance(lib.pf_alloc_count(), int)
