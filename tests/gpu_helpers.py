@@ -63,16 +63,20 @@ def perturbed_poses(P, K, max_deg, max_cm, seed):
     return out
 
 
-def compare_fitness(E_gpu, C_gpu, orc, rel=1e-5, floor=1e-7):
+def compare_fitness(E_gpu, C_gpu, orc, rel=1e-5, floor=0.0):
     """Element-wise check of GPU fitness against the oracle.
 
     The oracle leaves out the points lying on a cell face across which
     validity changes (FP32 and FP64 may put them on either side) and reports
     the value each would add.  The GPU count must be the oracle's plus some
     m of those points, and the GPU fitness must match, within `rel`, the
-    oracle's sum plus the values of some m of them, within `rel` plus an
-    absolute `floor` (the FP32 position-quantisation floor of near-perfect
-    alignments).  Returns the number of poses that had ambiguous points."""
+    oracle's sum plus the values of some m of them, within `rel` (1e-5, the
+    target's relative bound) plus an absolute `floor` -- zero for the
+    product layouts, whose sample positions are formed from exact reference
+    products (measured: at most 8.6e-7 relative over every parity case,
+    converged E ~ 0.004 included); only the plain float baseline, which
+    rounds each sample position at the scale of the grid coordinate, passes
+    a floor.  Returns the number of poses that had ambiguous points."""
     from itertools import combinations
     from math import comb
     K = len(orc.E)

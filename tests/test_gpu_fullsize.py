@@ -121,7 +121,7 @@ def test_fullsize_track(pf, fused, gpu_grid):
             break
         strict += 1
         assert st["best"][i] == os_["best"][i] and st["n_adv"][i] == os_["n_adv"][i], i
-        assert abs(st["E0"][i] - os_["E0"][i]) <= 1e-5 * os_["E0"][i] + 1e-7
+        assert abs(st["E0"][i] - os_["E0"][i]) <= 1e-5 * os_["E0"][i]
         np.testing.assert_allclose(st["s"][i], os_["s"][i], rtol=1e-5)
         np.testing.assert_allclose(st["pose"][i], os_["pose"][i], atol=1e-5)
     assert strict >= 1

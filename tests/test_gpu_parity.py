@@ -1,15 +1,13 @@
 """Parity of the CUDA path (through the C ABI) with the FP64 oracle.
 
-Tolerances (the figures the targets fix; the plain float baseline layout of
-the fitness has an absolute floor of 2e-6 instead of 1e-7, see
-test_fitness_parity):
+Tolerances (the figures the targets fix; only the plain float baseline layout
+of the fitness adds an absolute floor of 2e-6, see test_fitness_parity):
   back-projection  point count and order exact; coordinates within 3e-7
                    relative (two float roundings);
   fusion           weights exact, tsdf within 1e-5 (units of the truncation);
-  fitness          counts exact, E within 1e-5 relative plus 1e-7 absolute
-                   (FP32 quantisation of the sample positions: ~ulp(grid
-                   coordinate) / 2 per sample, averaged over the points, bounds
-                   the error of near-perfect alignments, E < 0.01);
+  fitness          counts exact, E within 1e-5 relative (the product layouts
+                   form sample positions from exact reference products; the
+                   largest error measured over every case is 8.6e-7);
   search           same best-particle index and advantage-set size while the
                    oracle's decision margins exceed 1e-5; final pose within
                    1e-4 m and 1e-4 rad.
@@ -193,7 +191,7 @@ def test_fitness_parity(pf, K, N, spread):
             # the plain float form rounds each sample position once at the
             # scale of the grid coordinate: up to ~ulp(64)/2 = 2e-6 voxel per
             # coordinate, i.e. |dt| <= ~3 x 2e-6 x (vs / tau) = 2e-6 per sample
-            compare_fitness(*results[layout, mapping], orc, floor=2e-6 if layout == 1 else 1e-7)
+            compare_fitness(*results[layout, mapping], orc, floor=2e-6 if layout == 1 else 0.0)
         # the same mapping evaluates the same samples in the same order on
         # both layouts (the automatic mapping may differ between layouts)
         if mapping > 0:
@@ -325,7 +323,7 @@ def test_track_parity(pf, update_mode, compose_mode):
         assert st["best"][i] == os_["best"][i], i
         if os_["adv_margin"][i] > 3e-5:
             assert st["n_adv"][i] == os_["n_adv"][i], i
-        assert abs(st["E0"][i] - os_["E0"][i]) <= 1e-5 * os_["E0"][i] + 1e-7
+        assert abs(st["E0"][i] - os_["E0"][i]) <= 1e-5 * os_["E0"][i]
         np.testing.assert_allclose(st["s"][i], os_["s"][i], rtol=1e-5)
         np.testing.assert_allclose(st["pose"][i], os_["pose"][i], atol=1e-5)
     assert strict >= 2, "the oracle's first iterations should be unambiguous for this seed"
