@@ -62,6 +62,9 @@ def parse():
                     help="storage type of the TSDF and its cell view (arithmetic stays f32); "
                          "fp8 = e4m3 holding 256 x the value")
     ap.add_argument("--weight-u8", action="store_true", help="store fusion weights as uint8")
+    ap.add_argument("--search-dtype", default="same", choices=["same", "f16", "bf16", "fp8"],
+                    help="storage of the cell view the search reads: the tsdf's (same), or a narrow search view "
+                         "of the float master grid, rounded once per refresh (fusion stays float)")
     ap.add_argument("--cell-view", type=int, default=0, choices=[-1, 0, 1, 2],
                     help="cell view of the volumes: 0 automatic, 1 full, 2 narrow records only, -1 none")
     ap.add_argument("--schedule", default="fixed", choices=["fixed", "paper"],
@@ -73,6 +76,10 @@ def parse():
                     help="Gauss-Newton polish steps (pf_polish) after each frame's search, before fusion")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--oracle-frames", type=int, default=2,
+                    help="frames 1..n of the device pass re-run by the FP64 oracle (the same closed loop on the "
+                         "host: its own fusion and poses); the bench line reports the position differences and "
+                         "both trajectories' errors against ground truth (0: skip)")
     ap.add_argument("--ref-particles", type=int, default=192,
                     help="particles per reference-arm step (a bounded slice of one iteration)")
     ap.add_argument("--kernel", default=None,
@@ -88,6 +95,11 @@ def parse():
     ap.add_argument("--frames", type=int, default=300,
                     help="--kernel precision: length of the multiroom trajectory (30 Hz); --steps + 1 frames of it "
                          "are used")
+    ap.add_argument("--vs-oracle", type=int, default=0,
+                    help="--kernel precision: compare with the FP64 oracle instead of the f32 volume -- fusion of "
+                         "--steps + 1 frames at the true poses (TSDF RMS / max per storage type against the oracle's "
+                         "FP64 grid), then this many frames tracked once each on every storage type and by the "
+                         "oracle on its grid (per-frame pose difference)")
     ap.add_argument("--fusion-only", action="store_true",
                     help="--kernel precision: fuse every frame at its true pose and report the storage deviation "
                          "only (no tracking pass)")
@@ -257,6 +269,41 @@ def job_rate(units_per_rank: int, world: int, ms_max: float) -> float:
     return units_per_rank * world / (ms_max / 1e3)
 
 
+def oracle_closed_loop(seq, depths, rels, gt, poses, args, n: int) -> dict:
+    """The FP64 oracle re-runs frames 1..n of the device pass's loop on the
+    host (fusion of frame 0 at its true pose, then per frame the search from
+    P_(t-1) P_(t,t-1) and fusion at the pose found): the GPU's positions
+    against the oracle's, and both trajectories' errors against ground
+    truth over those frames."""
+    import oracle
+    import synth
+    f32 = lambda v: float(np.float32(v))
+    intr, grid = seq.intr, seq.grid
+    ointr = synth.Intrinsics(intr.width, intr.height, f32(intr.fx), f32(intr.fy), f32(intr.cx), f32(intr.cy),
+                             f32(intr.depth_min), f32(intr.depth_max))
+    ogrid = synth.Grid(grid.nx, grid.ny, grid.nz, f32(grid.voxel_size), f32(grid.trunc),
+                       tuple(f32(o) for o in grid.origin))
+    prm = oracle.TrackParams(n_iters=N_ITERS, k_sched=(K_PARTICLES,) * 3, decim_sched=(1, 1, 1), s0_deg=10.0,
+                             s0_cm=10.0, beta=0.1, update_mode=args.update_mode, compose_mode=args.compose_mode,
+                             min_valid_frac=0.05)
+    templ = synth.templates(K_PARTICLES, args.seed)
+    t0 = time.perf_counter()
+    vol = oracle.Volume(ogrid)
+    oracle.integrate(vol, depths[0], ointr, gt[0])
+    P = gt[0]
+    diff, e_gpu, e_orc = [], [], []
+    for f in range(1, n + 1):
+        P = oracle.track(vol, depths[f], ointr, templ, P @ rels[f], prm).pose
+        oracle.integrate(vol, depths[f], ointr, P)
+        diff.append(float(np.linalg.norm(poses[f][:3, 3] - P[:3, 3])))
+        e_gpu.append(float(np.linalg.norm(poses[f][:3, 3] - gt[f][:3, 3])))
+        e_orc.append(float(np.linalg.norm(P[:3, 3] - gt[f][:3, 3])))
+    rms = lambda e: 100 * float(np.sqrt(np.mean(np.square(e))))
+    return {"frames": n, "position_diff_mm": [1e3 * d for d in diff], "ate_cm_gpu": rms(e_gpu),
+            "ate_cm_oracle": rms(e_orc), "oracle_threads": oracle.num_threads(),
+            "seconds": time.perf_counter() - t0}
+
+
 def run_reference(args):
     """The oracle (plain C, FP64) as the reference arm.  One step is one timed
     slice of a frame's work: the fitness of --ref-particles particles over all
@@ -299,13 +346,24 @@ def run_reference(args):
 
 def storage_desc(args) -> str:
     view = {0: "", 1: ", full cell view", 2: ", narrow cell view", -1: ", no cell view"}[int(getattr(args, "cell_view", 0))]
-    return f"{getattr(args, 'tsdf_dtype', 'f32')} tsdf + {'u8' if getattr(args, 'weight_u8', False) else 'f32'} weight{view}"
+    sv = getattr(args, "search_dtype", "same")
+    search = "" if sv == "same" else f", {sv} search view of the float grid"
+    return (f"{getattr(args, 'tsdf_dtype', 'f32')} tsdf + {'u8' if getattr(args, 'weight_u8', False) else 'f32'} "
+            f"weight{view}{search}")
+
+
+def search_dtype(args) -> str:
+    """Storage type of the records the search reads."""
+    sv = getattr(args, "search_dtype", "same")
+    return args.tsdf_dtype if sv == "same" else sv
 
 
 def new_volume(pf, grid, args):
-    dt = {"f32": pf.PF_F32, "f16": pf.PF_F16, "bf16": pf.PF_BF16, "fp8": pf.PF_FP8E4M3}[args.tsdf_dtype]
-    return pf.Volume.from_grid(grid, tsdf_dtype=dt, weight_u8=int(args.weight_u8),
-                               cell_view=int(getattr(args, "cell_view", 0)))
+    codes = {"f32": pf.PF_F32, "f16": pf.PF_F16, "bf16": pf.PF_BF16, "fp8": pf.PF_FP8E4M3}
+    sv = getattr(args, "search_dtype", "same")
+    return pf.Volume.from_grid(grid, tsdf_dtype=codes[args.tsdf_dtype], weight_u8=int(args.weight_u8),
+                               cell_view=int(getattr(args, "cell_view", 0)),
+                               search_dtype=pf.PF_F32 if sv == "same" else codes[sv])
 
 
 def schedule(args):
@@ -406,7 +464,7 @@ def run_ours(args):
     torch.cuda.synchronize()
     barrier()
     pf.pf_set_kernel_timing(True)
-    for cls in ("fitness", "fitness1", "integrate", "backproject"):
+    for cls in ("fitness", "fitness1", "integrate", "refresh", "backproject"):
         pf.pf_kernel_timing(cls)
     clocks = ClockSampler(local)
     clocks.start()
@@ -424,7 +482,7 @@ def run_ours(args):
     launches = pf.pf_launch_count() - launches0
     clock_info = clocks.stop()
     ms = t_begin.elapsed_time(t_end)
-    kt = {cls: pf.pf_kernel_timing(cls) for cls in ("fitness", "fitness1", "integrate", "backproject")}
+    kt = {cls: pf.pf_kernel_timing(cls) for cls in ("fitness", "fitness1", "integrate", "refresh", "backproject")}
     pf.pf_set_kernel_timing(False)
     ms_max = max_over_ranks(ms, dist, dev)
 
@@ -443,7 +501,7 @@ def run_ours(args):
     # ---- fitness kernel throughput, encoded vs plain layout --------------
     # (the plain layout exists for float storage only)
     vs_plain = fitness_vs_plain(pf, vol, depth_dev[W + 1], intr, poses[W], dev) if args.tsdf_dtype == "f32" \
-        and not args.weight_u8 else None
+        and not args.weight_u8 and getattr(args, "search_dtype", "same") == "same" else None
 
     # ---- end-to-end pass through the host API ----------------------------
     e2e = None
@@ -457,7 +515,7 @@ def run_ours(args):
     achieved_tflops = samples_per_launch * FLOP_PER_SAMPLE / (fit_avg_ms / 1e3) / 1e12
     peak_tflops = fp32_peak_tflops()
     ceilings = gather_ceilings(pf, dev)
-    rec_bytes = RECORD_BYTES[args.tsdf_dtype]
+    rec_bytes = RECORD_BYTES[search_dtype(args)]
     achieved_gbs = samples_per_launch * rec_bytes / (fit_avg_ms / 1e3) / 1e9
     line = {
         "metric": METRIC, "value": value, "unit": "frames/s", "n_gpus": world, "steps": K, "warmup": W,
@@ -489,6 +547,10 @@ def run_ours(args):
     if rank == 0 and world == 1 and not args.no_cpu_baseline and args.schedule == "fixed":
         fps, desc, cores, times, t_int, npts = oracle_sample(seq, depths, rels, args.compose_mode, 1024, repeats=1)
         line["cpu_baseline"] = {"value": fps, "unit": "frames/s", "cores": cores, "kind": "oracle", "sample": desc}
+    if rank == 0 and args.oracle_frames > 0 and args.schedule == "fixed" and step == 1 and not args.polish \
+            and args.tsdf_dtype == "f32" and not args.weight_u8 and args.search_dtype == "same":
+        line["oracle_closed_loop"] = oracle_closed_loop(seq, depths, rels, gt, poses, args,
+                                                        min(args.oracle_frames, W + K))
     if rank == 0:
         print(json.dumps(line))
     vol.close()
@@ -1055,6 +1117,103 @@ def run_room64(args):
     return 0
 
 
+def run_precision_oracle(args):
+    """Reduced-precision storage at scale against the FP64 oracle (640x480
+    into 768^3 at 8 mm, tau 2.4 cm, uint8 weights, automatic cell view).
+    (a) Fusion of frames 0..--steps at their true poses by every storage type
+    and by the oracle in FP64: RMS and max of the stored tsdf minus the
+    oracle's over nodes observed by both, and whether the weights agree.
+    (b) For frames 1..--vs-oracle: the search of frame f (3072 particles x 20
+    iterations from P_(f-1) P_(f,f-1), perturbed) on each storage type's grid
+    and on the oracle's, both fused at the true poses of frames 0..f-1, then
+    frame f fused at its true pose: the per-frame difference of the found
+    poses from the oracle's, and each one's error against ground truth."""
+    import synth
+    import oracle
+    n = max(2, args.steps + 1)
+    n_pose = max(0, min(args.vs_oracle, n - 1))
+    n_traj = max(args.frames, n)
+    grid = synth.Grid(768, 768, 768, 0.008, 0.024, (-0.5, -0.5, -0.5))
+    seq = synth.multiroom_sequence(n_traj, args.seed, grid=grid)
+    import multiprocessing as mp
+    with mp.get_context("spawn").Pool(max(1, min(16, (os.cpu_count() or 2) - 1))) as pool:
+        out = pool.map(_render, [(n_traj, args.seed, f, 1) for f in range(n)])
+    depths = [o[0] for o in out]
+    rels = [o[1] for o in out]
+    import torch
+
+    import paper_2509_24236_gb300 as pf
+    from paper_2509_24236_gb300 import build as pfbuild
+    pfbuild.build()
+    pf.load()
+    dev = torch.device("cuda", 0)
+    intr = seq.intr
+    f32 = lambda v: float(np.float32(v))
+    ointr = synth.Intrinsics(intr.width, intr.height, f32(intr.fx), f32(intr.fy), f32(intr.cx), f32(intr.cy),
+                             f32(intr.depth_min), f32(intr.depth_max))
+    ogrid = synth.Grid(grid.nx, grid.ny, grid.nz, f32(grid.voxel_size), f32(grid.trunc),
+                       tuple(f32(o) for o in grid.origin))
+    templ_np = synth.templates(K_PARTICLES, args.seed)
+    templ = torch.from_numpy(templ_np).to(dev)
+    params = pf.track_params(templ, n_iters=N_ITERS, k_sched=(K_PARTICLES,) * 3, decim_sched=(1, 1, 1),
+                             update_mode=args.update_mode, compose_mode=args.compose_mode, min_valid_frac=0.05)
+    oparams = oracle.TrackParams(n_iters=N_ITERS, k_sched=(K_PARTICLES,) * 3, decim_sched=(1, 1, 1), s0_deg=10.0,
+                                 s0_cm=10.0, beta=0.1, update_mode=args.update_mode, compose_mode=args.compose_mode,
+                                 min_valid_frac=0.05)
+    dd = [torch.from_numpy(d).to(dev) for d in depths]
+    codes = {"f32": pf.PF_F32, "f16": pf.PF_F16, "bf16": pf.PF_BF16, "fp8": pf.PF_FP8E4M3}
+    # the oracle: per-frame searches on its grid fused at the true poses, then the remaining fusions
+    ovol = oracle.Volume(ogrid)
+    opose = {}
+    # nodes whose update, in some frame, sits within 1e-3 px of a pixel-rounding
+    # boundary or 1e-6 m of the -tau cut or the camera plane: FP32 and FP64 may
+    # take either side there (another pixel's depth), so they are counted apart
+    amb = np.zeros(grid.n_nodes, dtype=bool)
+    t0 = time.perf_counter()
+    for f in range(n):
+        if 1 <= f <= n_pose:
+            opose[f] = oracle.track(ovol, depths[f], ointr, templ_np, seq.gt[f - 1] @ rels[f], oparams).pose
+        amb |= oracle.integrate(ovol, depths[f], ointr, seq.gt[f], ambiguity=True).astype(bool)
+    t_oracle = time.perf_counter() - t0
+    res = {}
+    configs = (("f32", "f32"), ("f32", "f16"), ("f32", "bf16"), ("f16", "f16"), ("bf16", "bf16"), ("fp8", "fp8"))
+    for name, search in configs:
+        vol = pf.Volume.from_grid(grid, tsdf_dtype=codes[name], weight_u8=1,
+                                  search_dtype=pf.PF_F32 if search == name else codes[search])
+        vol.reserve(intr.width * intr.height, K_PARTICLES)
+        r = {"frames": {}}
+        for f in range(n):
+            if 1 <= f <= n_pose:
+                st, P, _ = vol.track_frame(dd[f], intr, params, seq.gt[f - 1] @ rels[f])
+                r["frames"][f] = {
+                    "diff_to_oracle_mm": 1e3 * float(np.linalg.norm(P[:3, 3] - opose[f][:3, 3])),
+                    "diff_to_oracle_rad": float(np.arccos(np.clip((np.trace(P[:3, :3].T @ opose[f][:3, :3]) - 1) / 2,
+                                                                  -1, 1))),
+                    "err_to_truth_cm": 100 * float(np.linalg.norm(P[:3, 3] - seq.gt[f][:3, 3])),
+                    "oracle_err_to_truth_cm": 100 * float(np.linalg.norm(opose[f][:3, 3] - seq.gt[f][:3, 3]))}
+            vol.integrate(dd[f], intr, seq.gt[f])
+        t, w = vol.download()
+        both = (w > 0) & (ovol.weight > 0)
+        clean = both & ~amb
+        diff = np.abs(t[clean].astype(np.float64) - ovol.tsdf[clean])
+        diff_all = np.abs(t[both].astype(np.float64) - ovol.tsdf[both])
+        r["tsdf_vs_oracle"] = {"rms": float(np.sqrt(np.mean(diff ** 2))), "max": float(diff.max()),
+                               "nodes": int(clean.sum()),
+                               "weights_equal": bool(np.array_equal(w[~amb].astype(np.float64), ovol.weight[~amb])),
+                               "ambiguous_nodes": int((both & amb).sum()),
+                               "rms_all_nodes": float(np.sqrt(np.mean(diff_all ** 2)))}
+        res[name + "+u8" + ("" if search == name else f" ({search} search view)")] = r
+        del t, w, diff, diff_all, both, clean
+        vol.close()
+    print(json.dumps({"kernel": "precision", "against": "FP64 oracle",
+                      "workload": f"multiroom 640x480 ({n_traj}-frame trajectory), {n} frames fused at their true "
+                                  f"poses, frames 1-{n_pose} each searched once (3072 particles x 20 iterations) on "
+                                  "grids fused at the true poses of the frames before; 768^3 TSDF @ 8 mm (tau 2.4 cm), "
+                                  "uint8 weights", "oracle_seconds": t_oracle, "oracle_threads": oracle.num_threads(),
+                      "results": res}))
+    return 0
+
+
 def run_precision(args):
     """Reduced-precision storage at scale: the multiroom trajectory (frames
     0..--steps) at 640x480 into a 768^3 TSDF at 8 mm (tau 2.4 cm), tsdf in
@@ -1170,7 +1329,7 @@ def main():
     if args.kernel == "probe":
         return run_probe(args)
     if args.kernel == "precision":
-        return run_precision(args)
+        return run_precision_oracle(args) if args.vs_oracle > 0 else run_precision(args)
     if args.kernel == "room64":
         return run_room64(args)
     if args.kernel == "batch":

@@ -93,7 +93,18 @@ typedef enum { PF_F32 = 0, PF_F16 = 1, PF_BF16 = 2, PF_FP8E4M3 = 3 } pf_dtype;
  * view when the whole volume (grid, weights, view) fits in half of the
  * device memory free at creation (decoding narrow records on load slows the
  * search once the particles converge), else the narrow view when that
- * fits, else none.  pf_volume_info reports the choice. */
+ * fits, else none.  pf_volume_info reports the choice.
+ * search_dtype: storage type of the records in the cell view, which is what
+ * the search (pf_track_frame, and pf_fitness with the default layout) reads.
+ * PF_F32 (0): the tsdf storage type.  PF_F16, PF_BF16 or PF_FP8E4M3 with a
+ * float grid: a narrow search view of the float master grid -- fusion keeps
+ * averaging in float, and every refresh of the view rounds the current node
+ * values into it once (to nearest; a value that rounds to +-1 becomes the
+ * outside-the-band code), so the search samples that rounded grid while
+ * fusion accumulates no rounding.  It needs a cell view (cell_view -1 is
+ * PF_ERR_INVALID_ARG; automatic takes the full view when it fits, else the
+ * narrow one, else fails with PF_ERR_OOM).  Any other combination with a
+ * narrower search type is PF_ERR_UNSUPPORTED. */
 typedef struct {
     int nx, ny, nz;
     float voxel_size;
@@ -103,6 +114,7 @@ typedef struct {
     int weight_u8;
     int max_weight;
     int cell_view;
+    pf_dtype search_dtype;
 } pf_volume_desc;
 
 /* Parameters of the randomized optimization (Sec. III-B, defaults Sec. IV-A:

@@ -30,7 +30,8 @@ class pf_intrinsics(C.Structure):
 class pf_volume_desc(C.Structure):
     _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int), ("voxel_size", C.c_float),
                 ("trunc", C.c_float), ("origin", C.c_float * 3), ("tsdf_dtype", C.c_int),
-                ("weight_u8", C.c_int), ("max_weight", C.c_int), ("cell_view", C.c_int)]
+                ("weight_u8", C.c_int), ("max_weight", C.c_int), ("cell_view", C.c_int),
+                ("search_dtype", C.c_int)]
 
 
 class pf_track_params(C.Structure):
@@ -387,16 +388,16 @@ class Volume:
     """A TSDF volume on the current CUDA device (owns pf_volume)."""
 
     def __init__(self, nx, ny, nz, voxel_size, trunc, origin=(0.0, 0.0, 0.0), max_weight=255, cell_view=0,
-                 stream=None, tsdf_dtype=PF_F32, weight_u8=0):
+                 stream=None, tsdf_dtype=PF_F32, weight_u8=0, search_dtype=PF_F32):
         self.desc = pf_volume_desc(nx, ny, nz, voxel_size, trunc, (C.c_float * 3)(*origin), tsdf_dtype, weight_u8,
-                                   max_weight, cell_view)
+                                   max_weight, cell_view, search_dtype)
         self.n_nodes = nx * ny * nz
         self.handle = pf_create_volume(self.desc, stream)
 
     @classmethod
-    def from_grid(cls, grid, max_weight=255, cell_view=0, tsdf_dtype=PF_F32, weight_u8=0):
+    def from_grid(cls, grid, max_weight=255, cell_view=0, tsdf_dtype=PF_F32, weight_u8=0, search_dtype=PF_F32):
         return cls(grid.nx, grid.ny, grid.nz, grid.voxel_size, grid.trunc, grid.origin, max_weight, cell_view,
-                   tsdf_dtype=tsdf_dtype, weight_u8=weight_u8)
+                   tsdf_dtype=tsdf_dtype, weight_u8=weight_u8, search_dtype=search_dtype)
 
     def close(self):
         if getattr(self, "handle", None):

@@ -131,6 +131,17 @@ struct pf_workspace {
 // tile by tile after fusion.
 constexpr int PF_TX = 32, PF_TY = 8, PF_TZ = 8;
 
+// Per-fusion tile lists (device memory, one slot per tile): the tiles that
+// survive the frustum cull with the camera-frame position of their first
+// node, and the tiles whose cell-view records must be rewritten.
+struct FusionList {
+    int* count = nullptr;         // [0] fused tiles, [1] tiles to refresh
+    int* tile = nullptr;          // fused tile indices
+    float4* base = nullptr;       // their first node in the camera frame: x, y, z hi, z lo
+    float* step = nullptr;        // 9: camera-frame step per node index along i, j, k
+    int* refresh_tile = nullptr;  // tiles to refresh
+};
+
 struct pf_volume {
     pf_volume_desc desc;
     int device = 0;
@@ -144,8 +155,23 @@ struct pf_volume {
     int tiles[3] = {0, 0, 0};
     int fitness_variant = 0;
     pf_status last_status = PF_OK;  // last failing status of a call on this volume
+    FusionList list;
     pf_workspace ws;
 };
+
+// Storage type of the cell view's records: the node array's, or the search
+// view type of a float grid (pf_volume_desc.search_dtype).
+inline pf_dtype pf_view_dtype(const pf_volume* v)
+{
+    return v->desc.search_dtype != PF_F32 ? v->desc.search_dtype : v->desc.tsdf_dtype;
+}
+
+// Type the fitness kernel is instantiated on for a layout: the cell view's
+// (layout 3) or the node array's (layouts 1 and 2).
+inline pf_dtype pf_fitness_dtype(const pf_volume* v, int layout)
+{
+    return layout == 3 ? pf_view_dtype(v) : v->desc.tsdf_dtype;
+}
 
 // --------------------------------------------------------------------------
 // Host helpers

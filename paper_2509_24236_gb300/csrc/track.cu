@@ -1435,13 +1435,14 @@ void launch_fitness(FitArgs a, int variant, const pf_volume* v, int chunks, cuda
     const float auto_threshold = layout == 3 ? kParticleLanesBelowCells : kParticleLanesBelowNodes;
     a.pm_threshold = mapping == 1 ? -1.0f : mapping == 2 ? INFINITY : auto_threshold;
     dim3 grid(chunks, a.n_ptiles);
+    const pf_dtype dt = pf_fitness_dtype(v, layout);  // the cell view's records, or the node array's values
     if (layout == 1)  // the plain baseline: float tsdf and weights
         fitness_kernel<SRC, 1, float><<<grid, FIT_THREADS, 0, s>>>(a);
-    else if (v->desc.tsdf_dtype == PF_F16)
+    else if (dt == PF_F16)
         launch_fitness_t<SRC, __half>(a, layout, grid, s);
-    else if (v->desc.tsdf_dtype == PF_BF16)
+    else if (dt == PF_BF16)
         launch_fitness_t<SRC, __nv_bfloat16>(a, layout, grid, s);
-    else if (v->desc.tsdf_dtype == PF_FP8E4M3)
+    else if (dt == PF_FP8E4M3)
         launch_fitness_t<SRC, __nv_fp8_e4m3>(a, layout, grid, s);
     else
         launch_fitness_t<SRC, float>(a, layout, grid, s);
@@ -1948,9 +1949,9 @@ pf_status pf_batch_create(int n, pf_volume* const* vols, const pf_intrinsics* in
         st = check_params(params + i);
         if (st != PF_OK) return st;
         if (vols[i]->device != vols[0]->device) return PF_ERR_INVALID_ARG;
-        if (vols[i]->desc.tsdf_dtype != vols[0]->desc.tsdf_dtype) return PF_ERR_UNSUPPORTED;
         const int layout = resolve_layout(vols[i]);
         if (layout == 1 || layout != resolve_layout(vols[0])) return PF_ERR_UNSUPPORTED;
+        if (pf_fitness_dtype(vols[i], layout) != pf_fitness_dtype(vols[0], layout)) return PF_ERR_UNSUPPORTED;
     }
     pf_batch* b = new pf_batch();
     b->n = n;
@@ -1958,7 +1959,7 @@ pf_status pf_batch_create(int n, pf_volume* const* vols, const pf_intrinsics* in
     b->intrs.assign(intrs, intrs + n);
     b->params.assign(params, params + n);
     b->layout = resolve_layout(vols[0]);
-    b->dtype = vols[0]->desc.tsdf_dtype;
+    b->dtype = pf_fitness_dtype(vols[0], b->layout);
     b->device = vols[0]->device;
     b->use_graph = use_graph != 0;
     size_t depth_total = 0;

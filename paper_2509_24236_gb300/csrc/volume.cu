@@ -50,88 +50,116 @@ struct IntegArgs {
     float radius;                       // bounding radius of a tile (+ margin)
     int* tile_stamp;                    // tiles not culled get *stamp_dev (null: no cell view)
     const int* stamp_dev;               // fusion counter on the device
+    int tiles[3];                       // fusion tiles per axis
+    FusionList list;                    // tiles that survive the cull, with their bases
 };
 
+// Starts a fusion: empties the tile lists and, with a cell view, advances the
+// fusion counter the tile stamps refer to (on the device, so a captured and
+// replayed launch sequence still marks each fusion apart).
+__global__ void fusion_begin_kernel(FusionList list, int* stamp_counter)
+{
+    if (threadIdx.x == 0) {
+        list.count[0] = 0;
+        list.count[1] = 0;
+        if (stamp_counter) *stamp_counter += 1;
+    }
+}
+
+// One thread per fusion tile of TX x TY x TZ nodes: the camera-frame
+// position of the tile's first node, X_c = R^T (X_w - t) with
+// X_w = origin + vs (i0, j0, k0), in FP64 -- kept as floats, the depth as a
+// hi + lo pair -- and the frustum cull of the tile's bounding sphere.  A tile
+// that survives is stamped and appended to the list (its position in the
+// list depends on scheduling; each tile's nodes are fused once whatever the
+// order, so the result does not).  Thread 0 also writes the per-index steps,
+// vs times the rows of R, which every tile shares.
+__global__ void __launch_bounds__(256) fusion_tiles_kernel(IntegArgs a)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const int n_tiles = a.tiles[0] * a.tiles[1] * a.tiles[2];
+    if (t >= n_tiles) return;
+    const int bx = t % a.tiles[0], by = (t / a.tiles[0]) % a.tiles[1], bz = t / (a.tiles[0] * a.tiles[1]);
+    const int i0 = bx * TX, j0 = by * TY, k0 = bz * TZ;
+    const double* P = a.pose_dev ? a.pose_dev : a.pose;
+    double Pl[12];
+    for (int q = 0; q < 12; ++q) Pl[q] = P[q];
+    const double Xw[3] = {a.origin[0] + a.vs * i0, a.origin[1] + a.vs * j0, a.origin[2] + a.vs * k0};
+    const double d[3] = {Xw[0] - Pl[3], Xw[1] - Pl[7], Xw[2] - Pl[11]};
+    double b[3], c[3], st[9];
+    for (int r = 0; r < 3; ++r) {
+        b[r] = Pl[r] * d[0] + Pl[4 + r] * d[1] + Pl[8 + r] * d[2];
+        st[r] = a.vs * Pl[r];          // step along i
+        st[3 + r] = a.vs * Pl[4 + r];  // step along j
+        st[6 + r] = a.vs * Pl[8 + r];  // step along k
+        c[r] = b[r] + 0.5 * (TX - 1) * st[r] + 0.5 * (TY - 1) * st[3 + r] + 0.5 * (TZ - 1) * st[6 + r];
+    }
+    if (t == 0)
+        for (int q = 0; q < 9; ++q) a.list.step[q] = (float)st[q];
+    const float cx = (float)c[0], cy = (float)c[1], cz = (float)c[2];
+    bool skip = (cz + a.radius <= 0.0f) || (cz - a.radius > a.zfar);
+    for (int p = 0; p < 4 && !skip; ++p) {
+        const float dd = a.plane[p][0] * cx + a.plane[p][1] * cy + a.plane[p][2] * cz;
+        if (dd < -a.radius) skip = true;
+    }
+    if (skip) return;
+    if (a.tile_stamp) a.tile_stamp[t] = *a.stamp_dev;
+    const float hi = (float)b[2];
+    const int slot = atomicAdd(a.list.count, 1);
+    a.list.tile[slot] = t;
+    a.list.base[slot] = make_float4((float)b[0], (float)b[1], hi, (float)(b[2] - (double)hi));
+}
+
+// Fusion of the listed tiles; a fixed grid of CTAs walks the list.  Thread
+// (tx, ty) of a tile owns the column of TZ nodes (i0 + tx, j0 + ty, k0 + dz).
 template <typename TS, typename TW>
 __global__ void __launch_bounds__(TX * TY, 4) integrate_kernel(IntegArgs a)
 {
     TS* const tsdf = static_cast<TS*>(a.tsdf);
     TW* const weight = static_cast<TW*>(a.weight);
-    __shared__ float s_base[4];
-    __shared__ float s_step[9];
-    __shared__ int s_skip;
-    const int i0 = blockIdx.x * TX, j0 = blockIdx.y * TY, k0 = blockIdx.z * TZ;
-    if (threadIdx.x == 0 && threadIdx.y == 0) {
-        // X_c = R^T (X_w - t) with X_w = origin + vs (i, j, k), in FP64 for
-        // the tile's first node; steps per index are vs * (rows of R)
-        const double* P = a.pose_dev ? a.pose_dev : a.pose;
-        double Pl[12];
-        for (int q = 0; q < 12; ++q) Pl[q] = P[q];
-        const double Xw[3] = {a.origin[0] + a.vs * i0, a.origin[1] + a.vs * j0, a.origin[2] + a.vs * k0};
-        const double d[3] = {Xw[0] - Pl[3], Xw[1] - Pl[7], Xw[2] - Pl[11]};
-        double b[3], c[3], st[9];
-        for (int r = 0; r < 3; ++r) {
-            b[r] = Pl[r] * d[0] + Pl[4 + r] * d[1] + Pl[8 + r] * d[2];
-            st[r] = a.vs * Pl[r];          // step along i
-            st[3 + r] = a.vs * Pl[4 + r];  // step along j
-            st[6 + r] = a.vs * Pl[8 + r];  // step along k
-            c[r] = b[r] + 0.5 * (TX - 1) * st[r] + 0.5 * (TY - 1) * st[3 + r] + 0.5 * (TZ - 1) * st[6 + r];
-        }
-        for (int q = 0; q < 9; ++q) s_step[q] = (float)st[q];
-        float hi = (float)b[2];
-        s_base[0] = (float)b[0];
-        s_base[1] = (float)b[1];
-        s_base[2] = hi;
-        s_base[3] = (float)(b[2] - (double)hi);
-        float cx = (float)c[0], cy = (float)c[1], cz = (float)c[2];
-        int skip = (cz + a.radius <= 0.0f) || (cz - a.radius > a.zfar);
-        for (int p = 0; p < 4 && !skip; ++p) {
-            float d = a.plane[p][0] * cx + a.plane[p][1] * cy + a.plane[p][2] * cz;
-            if (d < -a.radius) skip = 1;
-        }
-        s_skip = skip;
-        if (!skip && a.tile_stamp)
-            a.tile_stamp[blockIdx.x + gridDim.x * (blockIdx.y + (size_t)gridDim.y * blockIdx.z)] = *a.stamp_dev;
-    }
-    __syncthreads();
-    if (s_skip) return;
+    const int n_active = *a.list.count;
     const int tx = threadIdx.x, ty = threadIdx.y;
-    const int i = i0 + tx, j = j0 + ty;
-    if (i >= a.nx || j >= a.ny) return;
-    const float bx = s_base[0], by = s_base[1], bz_hi = s_base[2], bz_lo = s_base[3];
-    const float ai[3] = {s_step[0], s_step[1], s_step[2]};
-    const float aj[3] = {s_step[3], s_step[4], s_step[5]};
-    const float ak[3] = {s_step[6], s_step[7], s_step[8]};
+    const float ai[3] = {a.list.step[0], a.list.step[1], a.list.step[2]};
+    const float aj[3] = {a.list.step[3], a.list.step[4], a.list.step[5]};
+    const float ak[3] = {a.list.step[6], a.list.step[7], a.list.step[8]};
     const float lx = fmaf((float)tx, ai[0], (float)ty * aj[0]);
     const float ly = fmaf((float)tx, ai[1], (float)ty * aj[1]);
     const float lz = fmaf((float)tx, ai[2], (float)ty * aj[2]);
     const size_t plane_stride = (size_t)a.nx * a.ny;
-    size_t idx = (size_t)i + (size_t)a.nx * j + plane_stride * k0;
-    for (int dz = 0; dz < TZ; ++dz, idx += plane_stride) {
-        const int k = k0 + dz;
-        if (k >= a.nz) break;
-        const float fz = (float)dz;
-        const float xc = bx + fmaf(fz, ak[0], lx);
-        const float yc = by + fmaf(fz, ak[1], ly);
-        const float zl = bz_lo + fmaf(fz, ak[2], lz);
-        const float zc = bz_hi + zl;
-        if (!(zc > 0.0f)) continue;
-        const float inv = __frcp_rn(zc);
-        const float u = fmaf(a.cam.fx * xc, inv, a.cam.cx);
-        const float v = fmaf(a.cam.fy * yc, inv, a.cam.cy);
-        const float uf = floorf(u + 0.5f), vf = floorf(v + 0.5f);
-        if (!(uf >= 0.0f && uf < (float)a.cam.width && vf >= 0.0f && vf < (float)a.cam.height)) continue;
-        const float d = __ldg(a.depth + (size_t)vf * a.cam.width + (size_t)uf);
-        if (!pf_depth_usable(d, a.cam.dmin, a.cam.dmax)) continue;
-        const float sdf = (d - bz_hi) - zl;
-        if (sdf < -a.trunc) continue;
-        const float t = fminf(1.0f, __fdiv_rn(sdf, a.trunc));
-        const float w = pf_to_float(weight[idx]);
-        float tn = t;
-        if (w > 0.0f) tn = __fdiv_rn(fmaf(w, pf_decode(pf_to_float(tsdf[idx])), t), w + 1.0f);
-        const float wn = fminf(w + 1.0f, a.max_weight);
-        tsdf[idx] = pf_from_float<TS>(pf_encode(tn, wn));
-        weight[idx] = pf_from_float<TW>(wn);
+    for (int e = blockIdx.x; e < n_active; e += gridDim.x) {
+        const int t = a.list.tile[e];
+        const float4 base = a.list.base[e];
+        const int bx = t % a.tiles[0], by = (t / a.tiles[0]) % a.tiles[1], bz = t / (a.tiles[0] * a.tiles[1]);
+        const int i = bx * TX + tx, j = by * TY + ty, k0 = bz * TZ;
+        if (i >= a.nx || j >= a.ny) continue;
+        const float bx_ = base.x, by_ = base.y, bz_hi = base.z, bz_lo = base.w;
+        size_t idx = (size_t)i + (size_t)a.nx * j + plane_stride * k0;
+        for (int dz = 0; dz < TZ; ++dz, idx += plane_stride) {
+            const int k = k0 + dz;
+            if (k >= a.nz) break;
+            const float fz = (float)dz;
+            const float xc = bx_ + fmaf(fz, ak[0], lx);
+            const float yc = by_ + fmaf(fz, ak[1], ly);
+            const float zl = bz_lo + fmaf(fz, ak[2], lz);
+            const float zc = bz_hi + zl;
+            if (!(zc > 0.0f)) continue;
+            const float inv = __frcp_rn(zc);
+            const float u = fmaf(a.cam.fx * xc, inv, a.cam.cx);
+            const float v = fmaf(a.cam.fy * yc, inv, a.cam.cy);
+            const float uf = floorf(u + 0.5f), vf = floorf(v + 0.5f);
+            if (!(uf >= 0.0f && uf < (float)a.cam.width && vf >= 0.0f && vf < (float)a.cam.height)) continue;
+            const float d = __ldg(a.depth + (size_t)vf * a.cam.width + (size_t)uf);
+            if (!pf_depth_usable(d, a.cam.dmin, a.cam.dmax)) continue;
+            const float sdf = (d - bz_hi) - zl;
+            if (sdf < -a.trunc) continue;
+            const float tt = fminf(1.0f, __fdiv_rn(sdf, a.trunc));
+            const float w = pf_to_float(weight[idx]);
+            float tn = tt;
+            if (w > 0.0f) tn = __fdiv_rn(fmaf(w, pf_decode(pf_to_float(tsdf[idx])), tt), w + 1.0f);
+            const float wn = fminf(w + 1.0f, a.max_weight);
+            tsdf[idx] = pf_from_float<TS>(pf_encode(tn, wn));
+            weight[idx] = pf_from_float<TW>(wn);
+        }
     }
 }
 
@@ -165,7 +193,29 @@ struct RefreshArgs {
     const int* tile_stamp;
     const int* stamp_dev;
     int all;
+    int tiles[3];
+    FusionList list;  // list.refresh_tile / count[1]: the tiles to rewrite
 };
+
+// One thread per tile: a tile's cells are rewritten when the tile or one of
+// its neighbours along +x, +y, +z (whose nodes its cells reach) was fused by
+// the last fusion, or always (all).  Order of the list as in
+// fusion_tiles_kernel: any, with the same result.
+__global__ void __launch_bounds__(256) refresh_tiles_kernel(RefreshArgs a)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const int n_tiles = a.tiles[0] * a.tiles[1] * a.tiles[2];
+    if (t >= n_tiles) return;
+    const int bx = t % a.tiles[0], by = (t / a.tiles[0]) % a.tiles[1], bz = t / (a.tiles[0] * a.tiles[1]);
+    bool need = a.all != 0;
+    const int stamp = *a.stamp_dev;
+    for (int q = 0; q < 8 && !need; ++q) {
+        const int x = bx + (q & 1), y = by + ((q >> 1) & 1), z = bz + (q >> 2);
+        if (x < a.tiles[0] && y < a.tiles[1] && z < a.tiles[2])
+            need = a.tile_stamp[x + a.tiles[0] * (y + (size_t)a.tiles[1] * z)] == stamp;
+    }
+    if (need) a.list.refresh_tile[atomicAdd(a.list.count + 1, 1)] = t;
+}
 
 // One cell-view record.  Float storage: two float4 holding the corners with
 // the x-differences precomputed (v000, v100 - v000, v010, v110 - v010 |
@@ -205,34 +255,68 @@ __device__ inline void store_cell32(const T* p, size_t nx, size_t nxy, float* ce
     c[1] = make_float4(v001, pf_to_float(p[nxy + 1]) - v001, v011, pf_to_float(p[nxy + nx + 1]) - v011);
 }
 
-template <typename TS>
+// A float grid's node values rounded once into a narrower view (the search
+// view of a float master grid): the eight corners converted with the
+// storage rule (a value that rounds to +-1 becomes the outside-the-band
+// code), written as the narrow record, and with a full view also as the
+// float record formed from the rounded values -- the grid the search reads.
+template <typename TV>
+__device__ inline void store_cell_rounded(const float* p, size_t nx, size_t nxy, TV* cells, float* cells32,
+                                          size_t idx)
+{
+    static_assert(sizeof(TV) == 2 || sizeof(TV) == 1, "16- or 8-bit view");
+    const TV h[8] = {pf_from_float<TV>(p[0]),       pf_from_float<TV>(p[1]),        pf_from_float<TV>(p[nx]),
+                     pf_from_float<TV>(p[nx + 1]),  pf_from_float<TV>(p[nxy]),      pf_from_float<TV>(p[nxy + 1]),
+                     pf_from_float<TV>(p[nxy + nx]), pf_from_float<TV>(p[nxy + nx + 1])};
+    if (sizeof(TV) == 2)
+        reinterpret_cast<uint4*>(cells)[idx] = *reinterpret_cast<const uint4*>(h);
+    else
+        reinterpret_cast<uint2*>(cells)[idx] = *reinterpret_cast<const uint2*>(h);
+    if (cells32) {
+        float v[8];
+        for (int c = 0; c < 8; ++c) v[c] = pf_to_float(h[c]);
+        float4* c = reinterpret_cast<float4*>(cells32) + 2 * idx;
+        c[0] = make_float4(v[0], v[1] - v[0], v[2], v[3] - v[2]);
+        c[1] = make_float4(v[4], v[5] - v[4], v[6], v[7] - v[6]);
+    }
+}
+
+// TS: storage of the node array; TV: storage of the view (TS itself, or a
+// narrower type for the search view of a float grid).  A fixed grid of CTAs
+// walks the list of tiles to rewrite.
+template <typename TS, typename TV>
 __global__ void __launch_bounds__(TX * TY, 4) cells_refresh_kernel(RefreshArgs a)
 {
-    __shared__ int s_need;
-    if (threadIdx.x == 0 && threadIdx.y == 0) {
-        int need = a.all;
-        for (int q = 0; q < 8 && !need; ++q) {
-            const unsigned bx = blockIdx.x + (q & 1), by = blockIdx.y + ((q >> 1) & 1), bz = blockIdx.z + (q >> 2);
-            if (bx < gridDim.x && by < gridDim.y && bz < gridDim.z)
-                need = a.tile_stamp[bx + gridDim.x * (by + (size_t)gridDim.y * bz)] == *a.stamp_dev;
-        }
-        s_need = need;
-    }
-    __syncthreads();
-    if (!s_need) return;
-    const int i = blockIdx.x * TX + threadIdx.x, j = blockIdx.y * TY + threadIdx.y;
-    if (i >= a.nx - 1 || j >= a.ny - 1) return;
+    const int n_list = a.list.count[1];
     const TS* tsdf = static_cast<const TS*>(a.tsdf);
-    TS* cells = static_cast<TS*>(a.cells);
+    TV* cells = static_cast<TV*>(a.cells);
     const size_t nx = a.nx, nxy = (size_t)a.nx * a.ny;
-    for (int dz = 0; dz < TZ; ++dz) {
-        const int k = blockIdx.z * TZ + dz;
-        if (k >= a.nz - 1) break;
-        const size_t idx = i + nx * j + nxy * k;
-        store_cell(tsdf + idx, nx, nxy, cells, idx);
-        if constexpr (!std::is_same<TS, float>::value)
-            if (a.cells32) store_cell32(tsdf + idx, nx, nxy, a.cells32, idx);
+    for (int e = blockIdx.x; e < n_list; e += gridDim.x) {
+        const int t = a.list.refresh_tile[e];
+        const int bx = t % a.tiles[0], by = (t / a.tiles[0]) % a.tiles[1], bz = t / (a.tiles[0] * a.tiles[1]);
+        const int i = bx * TX + threadIdx.x, j = by * TY + threadIdx.y;
+        if (i >= a.nx - 1 || j >= a.ny - 1) continue;
+        for (int dz = 0; dz < TZ; ++dz) {
+            const int k = bz * TZ + dz;
+            if (k >= a.nz - 1) break;
+            const size_t idx = i + nx * j + nxy * k;
+            if constexpr (!std::is_same<TS, TV>::value) {
+                store_cell_rounded(tsdf + idx, nx, nxy, cells, a.cells32, idx);
+            } else {
+                store_cell(tsdf + idx, nx, nxy, cells, idx);
+                if constexpr (!std::is_same<TS, float>::value)
+                    if (a.cells32) store_cell32(tsdf + idx, nx, nxy, a.cells32, idx);
+            }
+        }
     }
+}
+
+// CTAs of the list-walking fusion and refresh kernels: 4 per SM.
+int list_ctas(int device)
+{
+    int sms = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess || sms <= 0) sms = 152;
+    return 4 * sms;
 }
 
 pf_status enqueue_refresh(pf_volume* v, cudaStream_t s, int all)
@@ -245,15 +329,33 @@ pf_status enqueue_refresh(pf_volume* v, cudaStream_t s, int all)
     r.nx = v->desc.nx;
     r.ny = v->desc.ny;
     r.nz = v->desc.nz;
+    const int n_tiles = v->tiles[0] * v->tiles[1] * v->tiles[2];
     r.tile_stamp = v->tile_stamp;
-    r.stamp_dev = v->tile_stamp + (size_t)v->tiles[0] * v->tiles[1] * v->tiles[2];
+    r.stamp_dev = v->tile_stamp + n_tiles;
     r.all = all;
-    dim3 grid(v->tiles[0], v->tiles[1], v->tiles[2]);
-    switch (v->desc.tsdf_dtype) {
-    case PF_F16: cells_refresh_kernel<__half><<<grid, dim3(TX, TY), 0, s>>>(r); break;
-    case PF_BF16: cells_refresh_kernel<__nv_bfloat16><<<grid, dim3(TX, TY), 0, s>>>(r); break;
-    case PF_FP8E4M3: cells_refresh_kernel<__nv_fp8_e4m3><<<grid, dim3(TX, TY), 0, s>>>(r); break;
-    default: cells_refresh_kernel<float><<<grid, dim3(TX, TY), 0, s>>>(r); break;
+    for (int q = 0; q < 3; ++q) r.tiles[q] = v->tiles[q];
+    r.list = v->list;
+    if (all) {  // outside a fusion: the list counter was not reset by fusion_begin_kernel
+        fusion_begin_kernel<<<1, 32, 0, s>>>(v->list, nullptr);
+        pf::count_launch();
+    }
+    refresh_tiles_kernel<<<(n_tiles + 255) / 256, 256, 0, s>>>(r);
+    pf::count_launch();
+    const int grid = list_ctas(v->device);
+    const dim3 blk(TX, TY);
+    if (v->desc.tsdf_dtype != pf_view_dtype(v)) {  // the search view of a float grid
+        switch (pf_view_dtype(v)) {
+        case PF_F16: cells_refresh_kernel<float, __half><<<grid, blk, 0, s>>>(r); break;
+        case PF_BF16: cells_refresh_kernel<float, __nv_bfloat16><<<grid, blk, 0, s>>>(r); break;
+        default: cells_refresh_kernel<float, __nv_fp8_e4m3><<<grid, blk, 0, s>>>(r); break;
+        }
+    } else {
+        switch (v->desc.tsdf_dtype) {
+        case PF_F16: cells_refresh_kernel<__half, __half><<<grid, blk, 0, s>>>(r); break;
+        case PF_BF16: cells_refresh_kernel<__nv_bfloat16, __nv_bfloat16><<<grid, blk, 0, s>>>(r); break;
+        case PF_FP8E4M3: cells_refresh_kernel<__nv_fp8_e4m3, __nv_fp8_e4m3><<<grid, blk, 0, s>>>(r); break;
+        default: cells_refresh_kernel<float, float><<<grid, blk, 0, s>>>(r); break;
+        }
     }
     pf::count_launch();
     PF_LAUNCHED();
@@ -291,7 +393,7 @@ struct FillLaunch {
 
 template <typename TS, typename TW>
 struct IntegrateLaunch {
-    static void run(dim3 grid, const IntegArgs& a, cudaStream_t s)
+    static void run(int grid, const IntegArgs& a, cudaStream_t s)
     {
         integrate_kernel<TS, TW><<<grid, dim3(TX, TY), 0, s>>>(a);
     }
@@ -314,6 +416,14 @@ pf_status check_desc(const pf_volume_desc* d)
     if (d->tsdf_dtype != PF_F32 && d->tsdf_dtype != PF_F16 && d->tsdf_dtype != PF_BF16 &&
         d->tsdf_dtype != PF_FP8E4M3)
         return PF_ERR_UNSUPPORTED;
+    // a search view narrower than the storage: float grids only, and it
+    // needs a cell view
+    if (d->search_dtype != PF_F32 && d->search_dtype != d->tsdf_dtype) {
+        if (d->search_dtype != PF_F16 && d->search_dtype != PF_BF16 && d->search_dtype != PF_FP8E4M3)
+            return PF_ERR_UNSUPPORTED;
+        if (d->tsdf_dtype != PF_F32) return PF_ERR_UNSUPPORTED;
+        if (d->cell_view == -1) return PF_ERR_INVALID_ARG;
+    }
     return PF_OK;
 }
 
@@ -323,6 +433,16 @@ pf_status enqueue_reset(pf_volume* v, cudaStream_t s)
     pf::count_launch();
     PF_LAUNCHED();
     return enqueue_refresh(v, s, 1);
+}
+
+void free_list(FusionList& l)
+{
+    cudaFree(l.count);
+    cudaFree(l.tile);
+    cudaFree(l.base);
+    cudaFree(l.step);
+    cudaFree(l.refresh_tile);
+    l = FusionList();
 }
 
 bool finite_pose(const double* P)
@@ -349,12 +469,14 @@ pf_status pf_create_volume(const pf_volume_desc* desc, void* stream, pf_volume**
     v->tiles[1] = (desc->ny + TY - 1) / TY;
     v->tiles[2] = (desc->nz + TZ - 1) / TZ;
     const size_t ts = pf_dtype_size(desc->tsdf_dtype), ws = desc->weight_u8 ? 1 : 4;
+    const pf_dtype vdt = pf_view_dtype(v);
+    const size_t vs = pf_dtype_size(vdt);
     // the full view of a 16-/8-bit grid keeps both its narrow records (lanes
     // on points: two or four records per sector) and float records (lanes on
     // particles: no conversions); the narrow view keeps the narrow records
     // only; a float grid has the float records only
-    const size_t bytes32 = desc->tsdf_dtype == PF_F32 ? 0 : v->n_nodes * 32;
-    const size_t view_bytes = v->n_nodes * 8 * ts;
+    const size_t bytes32 = vdt == PF_F32 ? 0 : v->n_nodes * 32;
+    const size_t view_bytes = v->n_nodes * 8 * vs;
     const size_t grid_bytes = v->n_nodes * (ts + ws);
     cudaError_t e = cudaGetDevice(&v->device);
     int mode = desc->cell_view;
@@ -368,12 +490,19 @@ pf_status pf_create_volume(const pf_volume_desc* desc, void* stream, pf_volume**
         mode = grid_bytes + view_bytes + bytes32 <= budget ? 1 : grid_bytes + view_bytes <= budget ? 2 : -1;
     }
     if (mode == 2 && !bytes32) mode = 1;
+    if (mode == -1 && vdt != desc->tsdf_dtype) e = cudaErrorMemoryAllocation;  // no room for the search view
     const bool view = mode >= 1;
     const bool wide = mode == 1;
     if (e == cudaSuccess) e = pf::dev_malloc(&v->tsdf, v->n_nodes * ts);
     if (e == cudaSuccess) e = pf::dev_malloc(&v->weight, v->n_nodes * ws);
     if (e == cudaSuccess && view) e = pf::dev_malloc(&v->cells, view_bytes);
     if (e == cudaSuccess && wide && bytes32) e = pf::dev_malloc(&v->cells32, bytes32);
+    const size_t n_tiles = (size_t)v->tiles[0] * v->tiles[1] * v->tiles[2];
+    if (e == cudaSuccess) e = pf::dev_malloc(&v->list.count, 2 * sizeof(int));
+    if (e == cudaSuccess) e = pf::dev_malloc(&v->list.tile, n_tiles * sizeof(int));
+    if (e == cudaSuccess) e = pf::dev_malloc(&v->list.base, n_tiles * sizeof(float4));
+    if (e == cudaSuccess) e = pf::dev_malloc(&v->list.step, 9 * sizeof(float));
+    if (e == cudaSuccess && view) e = pf::dev_malloc(&v->list.refresh_tile, n_tiles * sizeof(int));
     if (e == cudaSuccess && view)
         e = pf::dev_malloc(&v->tile_stamp, sizeof(int) * ((size_t)v->tiles[0] * v->tiles[1] * v->tiles[2] + 1));
     if (e == cudaSuccess && view)
@@ -384,6 +513,7 @@ pf_status pf_create_volume(const pf_volume_desc* desc, void* stream, pf_volume**
         cudaFree(v->cells);
         cudaFree(v->cells32);
         cudaFree(v->tile_stamp);
+        free_list(v->list);
         delete v;
         cudaGetLastError();
         return pf::cuda_status(e);
@@ -407,6 +537,7 @@ pf_status pf_destroy_volume(pf_volume* v)
     cudaFree(v->cells);
     cudaFree(v->cells32);
     cudaFree(v->tile_stamp);
+    free_list(v->list);
     pf_workspace& w = v->ws;
     cudaFree(w.points);
     cudaFree(w.block_counts);
@@ -440,13 +571,13 @@ static pf_status pf_set_fitness_variant_impl(pf_volume* v, int variant)
 pf_status pf_volume_info(const pf_volume* v, unsigned long long* storage_bytes, int* cell_view)
 {
     if (!v) return PF_ERR_INVALID_ARG;
-    const size_t n = v->n_nodes, ts = pf_dtype_size(v->desc.tsdf_dtype);
+    const size_t n = v->n_nodes, ts = pf_dtype_size(v->desc.tsdf_dtype), vs = pf_dtype_size(pf_view_dtype(v));
     const size_t n_tiles = (size_t)v->tiles[0] * v->tiles[1] * v->tiles[2];
     size_t b = n * ts + n * (v->desc.weight_u8 ? 1 : 4);
-    if (v->cells) b += n * 8 * ts + sizeof(int) * (n_tiles + 1);
+    if (v->cells) b += n * 8 * vs + sizeof(int) * (n_tiles + 1);
     if (v->cells32) b += n * 32;
     if (storage_bytes) *storage_bytes = b;
-    if (cell_view) *cell_view = !v->cells ? -1 : (v->cells32 || v->desc.tsdf_dtype == PF_F32) ? 1 : 2;
+    if (cell_view) *cell_view = !v->cells ? -1 : (v->cells32 || pf_view_dtype(v) == PF_F32) ? 1 : 2;
     return PF_OK;
 }
 
@@ -535,11 +666,6 @@ static pf_status pf_volume_download_impl(const pf_volume* v, float* tsdf_host, f
 
 namespace {
 
-__global__ void stamp_bump_kernel(int* counter)
-{
-    if (threadIdx.x == 0) *counter += 1;
-}
-
 pf_status integrate_impl(pf_volume* v, const float* depth_dev, const pf_intrinsics* intr, const double* P_host,
                          const double* P_dev, cudaStream_t s)
 {
@@ -575,19 +701,17 @@ pf_status integrate_impl(pf_volume* v, const float* depth_dev, const pf_intrinsi
                        + 0.01 * vs + 1e-3);
     // the fusion counter lives on the device (after the per-tile stamps), so
     // a captured and replayed launch sequence still marks each fusion apart
-    const size_t n_tiles = (size_t)v->tiles[0] * v->tiles[1] * v->tiles[2];
+    const int n_tiles = v->tiles[0] * v->tiles[1] * v->tiles[2];
     a.tile_stamp = v->tile_stamp;
     a.stamp_dev = v->tile_stamp ? v->tile_stamp + n_tiles : nullptr;
+    for (int q = 0; q < 3; ++q) a.tiles[q] = v->tiles[q];
+    a.list = v->list;
     ++v->stamp;
-    if (v->tile_stamp) {
-        stamp_bump_kernel<<<1, 1, 0, s>>>(v->tile_stamp + n_tiles);
-        pf::count_launch();
-        PF_LAUNCHED();
-    }
-    dim3 grid(v->tiles[0], v->tiles[1], v->tiles[2]);
     pf::timing_begin(pf::KC_INTEGRATE, s);
-    dispatch_storage<IntegrateLaunch>(v, grid, a, s);
-    pf::count_launch();
+    fusion_begin_kernel<<<1, 32, 0, s>>>(v->list, v->tile_stamp ? v->tile_stamp + n_tiles : nullptr);
+    fusion_tiles_kernel<<<(n_tiles + 255) / 256, 256, 0, s>>>(a);
+    dispatch_storage<IntegrateLaunch>(v, list_ctas(v->device), a, s);
+    pf::count_launch(3);
     pf::timing_end(pf::KC_INTEGRATE, s);
     PF_LAUNCHED();
     pf::timing_begin(pf::KC_REFRESH, s);

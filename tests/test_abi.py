@@ -76,6 +76,14 @@ def test_host_side_validation_without_a_gpu(lib):
     for dt, u8, mw in ((pf.PF_F16, 1, 256), (pf.PF_BF16, 2, 255), (pf.PF_F32, -1, 10)):
         d = pf.pf_volume_desc(8, 8, 8, 0.1, 0.3, (C.c_float * 3)(0, 0, 0), dt, u8, mw)
         assert lib.pf_create_volume(C.byref(d), None, C.byref(out)) == pf.PF_ERR_INVALID_ARG
+    # a search view narrower than the storage: float grids only, with a cell
+    # view, of a known type
+    for dt, view, search, want in ((pf.PF_F16, 0, pf.PF_BF16, pf.PF_ERR_UNSUPPORTED),
+                                   (pf.PF_BF16, 1, pf.PF_FP8E4M3, pf.PF_ERR_UNSUPPORTED),
+                                   (pf.PF_F32, 0, 9, pf.PF_ERR_UNSUPPORTED),
+                                   (pf.PF_F32, -1, pf.PF_F16, pf.PF_ERR_INVALID_ARG)):
+        d = pf.pf_volume_desc(8, 8, 8, 0.1, 0.3, (C.c_float * 3)(0, 0, 0), dt, 0, 255, view, search)
+        assert lib.pf_create_volume(C.byref(d), None, C.byref(out)) == want, (dt, view, search)
     # NULL volume / pointers
     intr = pf.pf_intrinsics(4, 3, 2.0, 2.0, 1.5, 1.0, 0.1, 8.0)
     pose = (C.c_double * 16)(*[1, 0, 0, 0, 0, 1, 0, 0, 0, 0, 1, 0, 0, 0, 0, 1])
