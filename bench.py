@@ -1009,6 +1009,7 @@ def run_batch(args):
         if use_graph:
             load(1)
             out["points_per_block"] = batch.autotune()
+            out["mapping_threshold"] = batch.tuning()["mapping_threshold"]
         for f in range(1, W + 1):
             load(f)
             batch.step()
@@ -1035,6 +1036,7 @@ def run_batch(args):
         "speedup_graph_vs_sequential": ms_seq / out["graph"],
         "speedup_graph_vs_plain_f32_sequential": ms_plain / out["graph"],
         "points_per_block": out.get("points_per_block"),
+        "mapping_threshold_voxels": out.get("mapping_threshold"),
         "max_position_difference_batch_vs_sequential_after_first_step_m": out.get("pose_diff_1_m"),
         "max_final_position_difference_batch_vs_sequential_m": out["pose_diff_m"],
     }))

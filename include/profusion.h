@@ -321,13 +321,21 @@ PF_API pf_status pf_raycast(const pf_volume* vol, const pf_intrinsics* intr, con
  * pf_batch_fuse fuses every sequence's depth at its current pose (the first
  * frame).  pf_batch_step enqueues one step on cuda_stream (the first step
  * with use_graph captures the graph on a private stream; later steps replay
- * it; nothing synchronises).  pf_batch_autotune picks the evaluated points
- * per thread block of the batched launches by timing the first search
- * iteration of the current frames (on copies of the search state, at the
- * initial and at a contracted search size); it synchronises and drops any
- * captured graph.  pf_batch_set_points_per_block sets that value directly
- * (>= 1024).  Errors: PF_ERR_INVALID_ARG for bad arguments (before any
- * allocation), PF_ERR_UNSUPPORTED for mixed storage types or layouts. */
+ * it; nothing synchronises).  pf_batch_autotune tunes two axes of the
+ * batched launches by timing the first search iteration of the current
+ * frames on copies of the search state: the evaluated points per thread
+ * block (at the initial and at a 1e-3 contracted search size), then the
+ * lane-mapping threshold -- the reach of a particle chunk, in voxels, below
+ * which particles take the lanes of a warp instead of points -- at search
+ * sizes 0.3, 0.1 and 0.03 of the initial one, where chunks change mapping
+ * (for sequences whose fitness variant leaves the mapping automatic; the
+ * mapping changes only the order of the float sums); it synchronises and
+ * drops any captured graph.  pf_batch_set_points_per_block (>= 1024) and
+ * pf_batch_set_mapping_threshold (voxels; <= 0: each volume's default, 5
+ * with a cell view and 12 without) set them directly; pf_batch_tuning
+ * reports both (threshold 0 = the defaults).  Errors: PF_ERR_INVALID_ARG for
+ * bad arguments (before any allocation), PF_ERR_UNSUPPORTED for mixed
+ * storage types or layouts. */
 typedef struct pf_batch pf_batch;
 PF_API pf_status pf_batch_create(int n, pf_volume* const* vols, const pf_intrinsics* intrs,
                                  const pf_track_params* params, int use_graph, pf_batch** out);
@@ -338,6 +346,8 @@ PF_API pf_status pf_batch_fuse(pf_batch* batch, void* cuda_stream);
 PF_API pf_status pf_batch_step(pf_batch* batch, void* cuda_stream);
 PF_API pf_status pf_batch_autotune(pf_batch* batch, void* cuda_stream, int* points_per_block_out);
 PF_API pf_status pf_batch_set_points_per_block(pf_batch* batch, int points_per_block);
+PF_API pf_status pf_batch_set_mapping_threshold(pf_batch* batch, float voxels);
+PF_API pf_status pf_batch_tuning(const pf_batch* batch, int* points_per_block, float* mapping_threshold);
 
 /* Alignment loss of n_frames poses against their frames' points, and its
  * derivatives -- the gradient counterpart of the fitness (Sec. III-B: the

@@ -67,7 +67,8 @@ EXPORTS = ["pf_create_volume", "pf_destroy_volume", "pf_reset_volume", "pf_volum
            "pf_track_reserve", "pf_raycast", "pf_set_fitness_variant", "pf_status_string", "pf_launch_count",
            "pf_set_kernel_timing", "pf_kernel_timing", "pf_align_loss", "pf_polish",
            "pf_batch_create", "pf_batch_destroy", "pf_batch_buffers", "pf_batch_fuse", "pf_batch_step",
-           "pf_batch_autotune", "pf_batch_set_points_per_block", "pf_volume_info", "pf_alloc_count", "pf_volume_last_error",
+           "pf_batch_autotune", "pf_batch_set_points_per_block", "pf_volume_info", "pf_alloc_count", "pf_volume_last_error", "pf_batch_set_mapping_threshold",
+           "pf_batch_tuning",
            "pf_gather_probe"]
 
 _lib = None
@@ -127,6 +128,8 @@ def load(path: str = LIB_PATH):
         "pf_batch_step": (st, [vp, vp]),
         "pf_batch_autotune": (st, [vp, vp, C.POINTER(C.c_int)]),
         "pf_batch_set_points_per_block": (st, [vp, C.c_int]),
+        "pf_batch_set_mapping_threshold": (st, [vp, C.c_float]),
+        "pf_batch_tuning": (st, [vp, C.POINTER(C.c_int), C.POINTER(C.c_float)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -584,6 +587,15 @@ class Batch:
 
     def set_points_per_block(self, p: int):
         _check(load().pf_batch_set_points_per_block(self.handle, int(p)), "pf_batch_set_points_per_block")
+
+    def set_mapping_threshold(self, voxels: float):
+        _check(load().pf_batch_set_mapping_threshold(self.handle, float(voxels)), "pf_batch_set_mapping_threshold")
+
+    def tuning(self) -> dict:
+        """{"points_per_block": ..., "mapping_threshold": ... (0 = each volume's default)}."""
+        p, t = C.c_int(), C.c_float()
+        _check(load().pf_batch_tuning(self.handle, C.byref(p), C.byref(t)), "pf_batch_tuning")
+        return {"points_per_block": p.value, "mapping_threshold": t.value}
 
     def stats_dict(self, i: int) -> dict:
         return pf_track_stats.from_buffer_copy(self.stats[i].cpu().numpy().tobytes()).to_dict()

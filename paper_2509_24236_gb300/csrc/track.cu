@@ -1733,6 +1733,9 @@ struct pf_batch {
     int* d_first = nullptr;
     std::vector<int> n_search, blocks_search, n_eval, blocks_eval;
     int points_per_block = 4096;
+    // lane-mapping threshold (voxels of chunk reach) of the sequences whose
+    // mapping is automatic; <= 0: each volume's default
+    float pm_threshold = 0.0f;
     // graph
     bool use_graph = false;
     cudaStream_t cap = nullptr;
@@ -1793,6 +1796,7 @@ FitArgs batch_args(const pf_batch* b, int i, SearchState* st, pf_track_stats* st
     a.counter = v->ws.counter;
     a.stats = stats;
     a.pm_threshold = mapping_threshold(v, b->layout);
+    if (b->pm_threshold > 0.0f && ((v->fitness_variant >> 2) & 3) == 0) a.pm_threshold = b->pm_threshold;
     return a;
 }
 
@@ -2078,11 +2082,33 @@ pf_status pf_batch_set_points_per_block(pf_batch* b, int points_per_block)
     return batch_tables(b, false);
 }
 
-// Times the batched search launch of iteration 0 on copies of the search
-// state, once with the initial search size (lanes on points) and once with
-// it scaled by 1e-3 (lanes on particles, the contracted search), for each
-// candidate points-per-CTA, and keeps the fastest (weights 1 : 3, about the
-// share of the two regimes in a 20-iteration search).
+pf_status pf_batch_set_mapping_threshold(pf_batch* b, float voxels)
+{
+    if (!b || !(voxels <= 1e6f)) return PF_ERR_INVALID_ARG;
+    PF_CUDA(cudaDeviceSynchronize());
+    b->pm_threshold = voxels > 0.0f ? voxels : 0.0f;
+    batch_drop_graph(b);
+    return batch_tables(b, false);
+}
+
+pf_status pf_batch_tuning(const pf_batch* b, int* points_per_block, float* mapping_threshold)
+{
+    if (!b) return PF_ERR_INVALID_ARG;
+    if (points_per_block) *points_per_block = b->points_per_block;
+    if (mapping_threshold) *mapping_threshold = b->pm_threshold;
+    return PF_OK;
+}
+
+// The autotuner's two axes, tuned one after the other on copies of the
+// search state (the first search iteration of the current frames):
+//   1. points per CTA of the batched launches, timed at the initial search
+//      size (lanes on points) and at 1e-3 of it (lanes on particles),
+//      weights 1 : 3 (about the two regimes' shares of a 20-iteration search);
+//   2. the lane-mapping threshold (voxels of a particle chunk's reach below
+//      which particles take the lanes), timed at search sizes 0.3, 0.1 and
+//      0.03 of the initial one, where chunks cross from one mapping to the
+//      other.
+// Each timing is the second of two runs (the first warms up).
 pf_status pf_batch_autotune(pf_batch* b, void* stream, int* chosen)
 {
     if (!b) return PF_ERR_INVALID_ARG;
@@ -2096,43 +2122,73 @@ pf_status pf_batch_autotune(pf_batch* b, void* stream, int* chosen)
     cudaEvent_t e0, e1;
     PF_CUDA(cudaEventCreate(&e0));
     PF_CUDA(cudaEventCreate(&e1));
-    const int candidates[] = {1024, 2048, 4096, 8192, 16384, 32768, 65536, 131072};
-    const int saved = b->points_per_block;
-    int best = saved;
-    float best_ms = INFINITY;
     pf_status st = PF_OK;
-    for (int c : candidates) {
-        b->points_per_block = c;
-        st = batch_tables(b, true);
-        if (st != PF_OK) break;
-        float total = 0.0f;
-        for (int regime = 0; regime < 2 && st == PF_OK; ++regime) {
-            const double f = regime == 0 ? 1.0 : 1e-3;
-            for (int rep = 0; rep < 2; ++rep) {  // the first run warms up
+    // total time of the first search iteration at the given search-size
+    // scales and weights, for the current tables
+    auto time_regimes = [&](const double* scale, const float* weight, int n_regimes, float& total) {
+        total = 0.0f;
+        for (int regime = 0; regime < n_regimes && st == PF_OK; ++regime) {
+            for (int rep = 0; rep < 2; ++rep) {
                 for (int i = 0; i < b->n; ++i)
-                    track_begin_kernel<<<1, 32, 0, s>>>(b->tune_state + i, b->pose(i), b->params[i].init_rot_deg * f,
-                                                        b->params[i].init_trans_cm * f, b->tune_stats + i);
+                    track_begin_kernel<<<1, 32, 0, s>>>(b->tune_state + i, b->pose(i),
+                                                        b->params[i].init_rot_deg * scale[regime],
+                                                        b->params[i].init_trans_cm * scale[regime], b->tune_stats + i);
                 cudaEventRecord(e0, s);
                 launch_batch<SRC_SEARCH>(b, 0, 0, s);
                 cudaEventRecord(e1, s);
                 if (cudaEventSynchronize(e1) != cudaSuccess) {
                     st = PF_ERR_CUDA;
-                    break;
+                    return;
                 }
                 float ms = 0.0f;
                 cudaEventElapsedTime(&ms, e0, e1);
-                if (rep == 1) total += (regime == 0 ? 1.0f : 3.0f) * ms;
+                if (rep == 1) total += weight[regime] * ms;
             }
         }
+    };
+    const int saved = b->points_per_block;
+    const float saved_pm = b->pm_threshold;
+    int best = saved;
+    float best_ms = INFINITY;
+    const int candidates[] = {1024, 2048, 4096, 8192, 16384, 32768, 65536, 131072};
+    const double scale1[2] = {1.0, 1e-3};
+    const float weight1[2] = {1.0f, 3.0f};
+    for (int c : candidates) {
+        b->points_per_block = c;
+        st = batch_tables(b, true);
+        if (st != PF_OK) break;
+        float total = 0.0f;
+        time_regimes(scale1, weight1, 2, total);
         if (st != PF_OK) break;
         if (total < best_ms) {
             best_ms = total;
             best = c;
         }
     }
+    b->points_per_block = st == PF_OK ? best : saved;
+    float best_pm = saved_pm;
+    if (st == PF_OK) {
+        const float thresholds[] = {0.0f, 2.0f, 3.0f, 8.0f, 12.0f, 20.0f};  // 0: each volume's default
+        const double scale2[3] = {0.3, 0.1, 0.03};
+        const float weight2[3] = {1.0f, 1.0f, 1.0f};
+        float best_t = INFINITY;
+        for (float t : thresholds) {
+            b->pm_threshold = t;
+            st = batch_tables(b, true);
+            if (st != PF_OK) break;
+            float total = 0.0f;
+            time_regimes(scale2, weight2, 3, total);
+            if (st != PF_OK) break;
+            if (total < best_t) {
+                best_t = total;
+                best_pm = t;
+            }
+        }
+    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    b->points_per_block = st == PF_OK ? best : saved;
+    if (st != PF_OK) b->points_per_block = saved;
+    b->pm_threshold = st == PF_OK ? best_pm : saved_pm;
     batch_drop_graph(b);
     pf_status st2 = batch_tables(b, false);
     if (chosen) *chosen = b->points_per_block;

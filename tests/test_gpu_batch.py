@@ -207,12 +207,23 @@ def test_autotune_and_validation(pf):
     batch.step()  # captures
     p = batch.autotune()
     assert p in (1024, 2048, 4096, 8192, 16384, 32768, 65536, 131072)
+    tuned = batch.tuning()
+    assert tuned["points_per_block"] == p and tuned["mapping_threshold"] in (0.0, 2.0, 3.0, 8.0, 12.0, 20.0)
     batch.step()  # recaptures with the chosen tiling
+    torch.cuda.synchronize()
+    # a forced threshold changes only which lanes carry which samples: the
+    # step still runs and reports the value back
+    batch.set_mapping_threshold(1e6)
+    assert batch.tuning()["mapping_threshold"] == 1e6
+    batch.set_mapping_threshold(0.0)
+    assert batch.tuning()["mapping_threshold"] == 0.0
     torch.cuda.synchronize()
     for i in range(batch.n):
         assert batch.stats_dict(i)["status"] == pf.PF_OK
     with pytest.raises(pf.ProfusionError):
         batch.set_points_per_block(100)
+    with pytest.raises(pf.ProfusionError):
+        batch.set_mapping_threshold(float("nan"))
     batch.close()
     # a volume may appear once; storage types may not mix
     with pytest.raises(pf.ProfusionError):

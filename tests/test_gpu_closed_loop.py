@@ -5,7 +5,8 @@ The bench's device-resident frame loop -- P_t^(0) = P_(t-1) P_(t,t-1)
 (pf_track_frame_async: 3072 particles x 20 iterations over all points,
 advantage-set mean update, Sec. III-B) and fusion at the result
 (pf_integrate_async, Sec. III) -- runs on the 640x480 / 512^3 multiroom
-workload for frames 1-5, and the oracle runs the same loop on the host in
+workload for frames 1-5, in the float form and with a half-precision search
+view of the float grid, and the oracle runs the same loop on the host in
 FP64 (its own fusion, its own poses).  Each frame's pose must stay within
 1 mm and 1e-3 rad of the oracle's, so the trajectory error the bench reports
 (ate_cm) is the method's, not the kernels': the two ATEs against ground
@@ -25,18 +26,11 @@ N_TRACKED = 5
 K = 3072
 
 
-def test_closed_loop_follows_the_oracle_at_full_size():
-    torch = torch_cuda()
-    pf = load_pf()
-    seq = synth.multiroom_sequence(300, 0)
+def _gpu_loop(pf, torch, seq, depths, rels, templ, search_dtype):
+    """The bench's device-resident loop on the GPU; poses of frames 0..N."""
     intr, grid = seq.intr, seq.grid
-    depths = [seq.depth(f) for f in range(N_TRACKED + 1)]
-    rels = [np.eye(4)] + [seq.relative_init(f) for f in range(1, N_TRACKED + 1)]
-    templ = synth.templates(K, 0)
-
-    # GPU: the bench's device-resident loop
     dev = torch.device("cuda", 0)
-    vol = pf.Volume.from_grid(grid)
+    vol = pf.Volume.from_grid(grid, search_dtype=search_dtype)
     params = pf.track_params(torch.from_numpy(templ).to(dev), n_iters=20, k_sched=(K,) * 3, decim_sched=(1,) * 3,
                              update_mode=0, compose_mode=1, min_valid_frac=0.05)
     vol.reserve(intr.width * intr.height, K)
@@ -51,8 +45,24 @@ def test_closed_loop_follows_the_oracle_at_full_size():
         vol.track_frame_async(depth_dev[f], intr, params, init_dev[f], pose_dev[f])
         vol.integrate_async(depth_dev[f], intr, pose_dev[f])
     torch.cuda.synchronize()
-    gpu = pose_dev.cpu().numpy().reshape(-1, 4, 4)
+    out = pose_dev.cpu().numpy().reshape(-1, 4, 4)
     vol.close()
+    return out
+
+
+def test_closed_loop_follows_the_oracle_at_full_size():
+    """The float form, and the reduced-precision form with a half-precision
+    search view of the float grid (fusion float, search on the grid rounded
+    once per refresh), against the same FP64 oracle loop."""
+    torch = torch_cuda()
+    pf = load_pf()
+    seq = synth.multiroom_sequence(300, 0)
+    intr, grid = seq.intr, seq.grid
+    depths = [seq.depth(f) for f in range(N_TRACKED + 1)]
+    rels = [np.eye(4)] + [seq.relative_init(f) for f in range(1, N_TRACKED + 1)]
+    templ = synth.templates(K, 0)
+    runs = {"f32": _gpu_loop(pf, torch, seq, depths, rels, templ, pf.PF_F32),
+            "f32 + f16 search view": _gpu_loop(pf, torch, seq, depths, rels, templ, pf.PF_F16)}
 
     # oracle: the same loop in FP64
     ovol = oracle.Volume(abi(grid))
@@ -68,13 +78,16 @@ def test_closed_loop_follows_the_oracle_at_full_size():
         orc.append(P)
         oracle.integrate(ovol, depths[f], abi(intr), P)
 
-    dt = [pose_trans_err(gpu[f], orc[f]) for f in range(1, N_TRACKED + 1)]
-    dr = [pose_rot_err(gpu[f], orc[f]) for f in range(1, N_TRACKED + 1)]
-    assert max(dt) <= 1e-3, dt
-    assert max(dr) <= 1e-3, dr
     ate = lambda poses: float(np.sqrt(np.mean([np.sum((poses[f][:3, 3] - seq.gt[f][:3, 3]) ** 2)
                                                for f in range(1, N_TRACKED + 1)])))
-    ate_gpu, ate_orc = ate(gpu), ate(orc)
-    assert abs(ate_gpu - ate_orc) <= 1e-3, (ate_gpu, ate_orc)
-    print(f"closed loop, frames 1-{N_TRACKED}: GPU vs oracle position difference max {1e3 * max(dt):.4f} mm, "
-          f"rotation max {max(dr):.2e} rad; ATE GPU {100 * ate_gpu:.3f} cm, oracle {100 * ate_orc:.3f} cm")
+    ate_orc = ate(orc)
+    for name, gpu in runs.items():
+        dt = [pose_trans_err(gpu[f], orc[f]) for f in range(1, N_TRACKED + 1)]
+        dr = [pose_rot_err(gpu[f], orc[f]) for f in range(1, N_TRACKED + 1)]
+        assert max(dt) <= 1e-3, (name, dt)
+        assert max(dr) <= 1e-3, (name, dr)
+        ate_gpu = ate(gpu)
+        assert abs(ate_gpu - ate_orc) <= 1e-3, (name, ate_gpu, ate_orc)
+        print(f"closed loop ({name}), frames 1-{N_TRACKED}: GPU vs oracle position difference max "
+              f"{1e3 * max(dt):.4f} mm, rotation max {max(dr):.2e} rad; ATE GPU {100 * ate_gpu:.3f} cm, "
+              f"oracle {100 * ate_orc:.3f} cm")
