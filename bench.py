@@ -1253,8 +1253,11 @@ def run_precision(args):
                              update_mode=args.update_mode, compose_mode=args.compose_mode, min_valid_frac=0.05)
     rel_dev = torch.from_numpy(np.stack([r.reshape(16) for r in rels])).to(dev)
     res, ref_tsdf, ref_w, ref_traj = {}, None, None, None
-    for name, view in (("f32", 0), ("f16", 0), ("f16", 2), ("bf16", 0), ("bf16", 2), ("fp8", 0), ("fp8", 2)):
-        vol = pf.Volume.from_grid(grid, tsdf_dtype=codes[name], weight_u8=1, cell_view=view)
+    configs = (("f32", 0, None), ("f32", 0, "f16"), ("f32", 0, "bf16"), ("f16", 0, None), ("f16", 2, None),
+               ("bf16", 0, None), ("bf16", 2, None), ("fp8", 0, None), ("fp8", 2, None))
+    for name, view, search in configs:
+        vol = pf.Volume.from_grid(grid, tsdf_dtype=codes[name], weight_u8=1, cell_view=view,
+                                  search_dtype=codes[search] if search else pf.PF_F32)
         info = vol.info()
         for f in range(n):
             vol.integrate(dd[f], intr, seq.gt[f])
@@ -1269,8 +1272,9 @@ def run_precision(args):
             r["tsdf_vs_f32"] = {"rms": float(np.sqrt(np.mean(diff ** 2))), "max": float(diff.max()),
                                 "nodes": int(both.sum()), "weights_equal": bool(np.array_equal(w, ref_w))}
         del t, w
+        key = name + "+u8" + ("+narrow" if view == 2 else "") + (f" ({search} search view)" if search else "")
         if args.fusion_only:
-            res[name + "+u8" + ("+narrow" if view == 2 else "")] = r
+            res[key] = r
             vol.close()
             continue
         vol.reset()
@@ -1297,7 +1301,7 @@ def run_precision(args):
         else:
             r["max_position_difference_to_f32_cm"] = 100 * float(np.max(np.linalg.norm(P[1:, :3, 3] - ref_traj[1:, :3, 3],
                                                                                        axis=1)))
-        res[name + "+u8" + ("+narrow" if view == 2 else "")] = r
+        res[key] = r
         vol.close()
     what = f"{n} frames fused at their true poses" if args.fusion_only else f"{n - 1} tracked frames"
     print(json.dumps({"kernel": "precision", "workload": f"multiroom 640x480 ({n_traj}-frame trajectory), {what}, "
