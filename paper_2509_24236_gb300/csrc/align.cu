@@ -770,9 +770,10 @@ void align_release(const pf_volume* v)
 
 extern "C" {
 
-static pf_status pf_align_loss_impl(const pf_volume* v, const float* points_dev, const int* counts_dev, int n_max, int n_frames,
-                        const double* poses_dev, const double* xi_dev, const double* dloss_dev, double* loss_dev,
-                        int* count_dev, double* grad_xi_dev, float* grad_tsdf_dev, void* stream)
+static pf_status pf_align_loss_impl(const pf_volume* v, const float* points_dev, const int* counts_dev, int n_max,
+                                    int n_frames, const double* poses_dev, const double* xi_dev,
+                                    const double* dloss_dev, double* loss_dev, int* count_dev, double* grad_xi_dev,
+                                    float* grad_tsdf_dev, void* stream)
 {
     if (!v || !poses_dev || !loss_dev || n_frames < 1 || n_max < 0 || n_frames > 65535) return PF_ERR_INVALID_ARG;
     if (n_max > 0 && !points_dev) return PF_ERR_INVALID_ARG;
@@ -826,8 +827,8 @@ static pf_status pf_align_loss_impl(const pf_volume* v, const float* points_dev,
     return PF_OK;
 }
 
-static pf_status pf_polish_impl(const pf_volume* v, const float* points_dev, const int* n_dev, int n_max, double* pose_dev,
-                    int steps, double* trace_dev, int* accepted_dev, void* stream)
+static pf_status pf_polish_impl(const pf_volume* v, const float* points_dev, const int* n_dev, int n_max,
+                                double* pose_dev, int steps, double* trace_dev, int* accepted_dev, void* stream)
 {
     if (!v || !pose_dev || n_max < 0 || steps < 0 || steps > 1000) return PF_ERR_INVALID_ARG;
     if (n_max > 0 && !points_dev) return PF_ERR_INVALID_ARG;
@@ -872,14 +873,19 @@ static pf_status pf_polish_impl(const pf_volume* v, const float* points_dev, con
 // there (pf_volume_last_error).
 extern "C" {
 
-pf_status pf_align_loss(const pf_volume* v, const float* points_dev, const int* counts_dev, int n_max, int n_frames, const double* poses_dev, const double* xi_dev, const double* dloss_dev, double* loss_dev, int* count_dev, double* grad_xi_dev, float* grad_tsdf_dev, void* stream)
+pf_status pf_align_loss(const pf_volume* v, const float* points_dev, const int* counts_dev, int n_max, int n_frames,
+                        const double* poses_dev, const double* xi_dev, const double* dloss_dev, double* loss_dev,
+                        int* count_dev, double* grad_xi_dev, float* grad_tsdf_dev, void* stream)
 {
-    return pf::keep_status(v, pf_align_loss_impl(v, points_dev, counts_dev, n_max, n_frames, poses_dev, xi_dev, dloss_dev, loss_dev, count_dev, grad_xi_dev, grad_tsdf_dev, stream));
+    return pf::keep_status(v, pf_align_loss_impl(v, points_dev, counts_dev, n_max, n_frames, poses_dev, xi_dev,
+                                                 dloss_dev, loss_dev, count_dev, grad_xi_dev, grad_tsdf_dev, stream));
 }
 
-pf_status pf_polish(const pf_volume* v, const float* points_dev, const int* n_dev, int n_max, double* pose_dev, int steps, double* trace_dev, int* accepted_dev, void* stream)
+pf_status pf_polish(const pf_volume* v, const float* points_dev, const int* n_dev, int n_max, double* pose_dev,
+                    int steps, double* trace_dev, int* accepted_dev, void* stream)
 {
-    return pf::keep_status(v, pf_polish_impl(v, points_dev, n_dev, n_max, pose_dev, steps, trace_dev, accepted_dev, stream));
+    return pf::keep_status(v, pf_polish_impl(v, points_dev, n_dev, n_max, pose_dev, steps, trace_dev, accepted_dev,
+                                             stream));
 }
 
 }  // extern "C"

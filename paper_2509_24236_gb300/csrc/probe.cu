@@ -83,9 +83,11 @@ extern "C" pf_status pf_gather_probe(const float* buf_dev, long long n_records, 
     if (!buf_dev) return PF_ERR_INVALID_ARG;
     cudaStream_t s = (cudaStream_t)stream;
     if (mode == 0)
-        gather_probe_kernel<0><<<blocks, PROBE_THREADS, 0, s>>>(buf_dev, (unsigned)n_records, loads_per_thread, out_dev);
+        gather_probe_kernel<0><<<blocks, PROBE_THREADS, 0, s>>>(buf_dev, (unsigned)n_records, loads_per_thread,
+                                                                out_dev);
     else
-        gather_probe_kernel<1><<<blocks, PROBE_THREADS, 0, s>>>(buf_dev, (unsigned)n_records, loads_per_thread, out_dev);
+        gather_probe_kernel<1><<<blocks, PROBE_THREADS, 0, s>>>(buf_dev, (unsigned)n_records, loads_per_thread,
+                                                                out_dev);
     pf::count_launch();
     PF_LAUNCHED();
     return PF_OK;

@@ -114,8 +114,8 @@ __global__ void raycast_kernel(RayArgs a)
 
 }  // namespace
 
-static pf_status pf_raycast_impl(const pf_volume* v, const pf_intrinsics* intr, const double P[16],
-                                float* depth_out, float* normal_out, void* stream)
+static pf_status pf_raycast_impl(const pf_volume* v, const pf_intrinsics* intr, const double P[16], float* depth_out,
+                                 float* normal_out, void* stream)
 {
     if (!v || !P || !depth_out) return PF_ERR_INVALID_ARG;
     pf_status st = pf::check_intrinsics(intr);
@@ -162,7 +162,8 @@ static pf_status pf_raycast_impl(const pf_volume* v, const pf_intrinsics* intr, 
 // there (pf_volume_last_error).
 extern "C" {
 
-pf_status pf_raycast(const pf_volume* v, const pf_intrinsics* intr, const double P[16], float* depth_out, float* normal_out, void* stream)
+pf_status pf_raycast(const pf_volume* v, const pf_intrinsics* intr, const double P[16], float* depth_out,
+                     float* normal_out, void* stream)
 {
     return pf::keep_status(v, pf_raycast_impl(v, intr, P, depth_out, normal_out, stream));
 }

@@ -1568,7 +1568,7 @@ pf_status pf_backproject(const float* depth_dev, const pf_intrinsics* intr, floa
 }
 
 static pf_status pf_fitness_impl(const pf_volume* cv, const float* points_dev, int n, const float* poses_dev, int k,
-                     float* fitness_dev, int* count_dev, void* stream)
+                                 float* fitness_dev, int* count_dev, void* stream)
 {
     pf_volume* v = const_cast<pf_volume*>(cv);
     if (!v || !poses_dev || !fitness_dev || !count_dev) return PF_ERR_INVALID_ARG;
@@ -1606,8 +1606,8 @@ static pf_status pf_track_reserve_impl(pf_volume* v, int max_pixels, int k_max)
 }
 
 static pf_status pf_track_frame_async_impl(pf_volume* v, const float* depth_dev, const pf_intrinsics* intr,
-                               const pf_track_params* p, const double* init_pose_dev, double* out_pose_dev,
-                               pf_track_stats* stats_dev, void* stream)
+                                           const pf_track_params* p, const double* init_pose_dev,
+                                           double* out_pose_dev, pf_track_stats* stats_dev, void* stream)
 {
     if (!v || !depth_dev || !init_pose_dev || !out_pose_dev) return PF_ERR_INVALID_ARG;
     pf_status st = pf::check_intrinsics(intr);
@@ -1672,9 +1672,9 @@ static pf_status pf_track_frame_async_impl(pf_volume* v, const float* depth_dev,
     return PF_OK;
 }
 
-static pf_status pf_track_frame_impl(pf_volume* v, const float* depth_dev, const pf_intrinsics* intr, const pf_track_params* p,
-                         const double init_pose[16], double out_pose[16], pf_track_stats* stats_host,
-                         void* stream)
+static pf_status pf_track_frame_impl(pf_volume* v, const float* depth_dev, const pf_intrinsics* intr,
+                                     const pf_track_params* p, const double init_pose[16], double out_pose[16],
+                                     pf_track_stats* stats_host, void* stream)
 {
     if (!v || !init_pose || !out_pose) return PF_ERR_INVALID_ARG;
     for (int q = 0; q < 12; ++q)
@@ -2277,7 +2277,7 @@ pf_status noalloc_scratch(int device, NoAllocScratch** out)
 }  // namespace
 
 static pf_status pf_fitness_noalloc_impl(const pf_volume* v, const float* points_dev, int n, const float* poses_dev,
-                                        int k, float* fitness_dev, int* count_dev, void* stream)
+                                         int k, float* fitness_dev, int* count_dev, void* stream)
 {
     if (!v || !poses_dev || !fitness_dev || !count_dev) return PF_ERR_INVALID_ARG;
     if (n < 0 || k < 1 || (n > 0 && !points_dev)) return PF_ERR_INVALID_ARG;
@@ -2315,7 +2315,8 @@ static pf_status pf_fitness_noalloc_impl(const pf_volume* v, const float* points
 // there (pf_volume_last_error).
 extern "C" {
 
-pf_status pf_fitness(const pf_volume* cv, const float* points_dev, int n, const float* poses_dev, int k, float* fitness_dev, int* count_dev, void* stream)
+pf_status pf_fitness(const pf_volume* cv, const float* points_dev, int n, const float* poses_dev, int k,
+                     float* fitness_dev, int* count_dev, void* stream)
 {
     return pf::keep_status(cv, pf_fitness_impl(cv, points_dev, n, poses_dev, k, fitness_dev, count_dev, stream));
 }
@@ -2325,19 +2326,25 @@ pf_status pf_track_reserve(pf_volume* v, int max_pixels, int k_max)
     return pf::keep_status(v, pf_track_reserve_impl(v, max_pixels, k_max));
 }
 
-pf_status pf_track_frame_async(pf_volume* v, const float* depth_dev, const pf_intrinsics* intr, const pf_track_params* p, const double* init_pose_dev, double* out_pose_dev, pf_track_stats* stats_dev, void* stream)
+pf_status pf_track_frame_async(pf_volume* v, const float* depth_dev, const pf_intrinsics* intr,
+                               const pf_track_params* p, const double* init_pose_dev, double* out_pose_dev,
+                               pf_track_stats* stats_dev, void* stream)
 {
-    return pf::keep_status(v, pf_track_frame_async_impl(v, depth_dev, intr, p, init_pose_dev, out_pose_dev, stats_dev, stream));
+    return pf::keep_status(v, pf_track_frame_async_impl(v, depth_dev, intr, p, init_pose_dev, out_pose_dev, stats_dev,
+                                                        stream));
 }
 
-pf_status pf_track_frame(pf_volume* v, const float* depth_dev, const pf_intrinsics* intr, const pf_track_params* p, const double init_pose[16], double out_pose[16], pf_track_stats* stats_host, void* stream)
+pf_status pf_track_frame(pf_volume* v, const float* depth_dev, const pf_intrinsics* intr, const pf_track_params* p,
+                         const double init_pose[16], double out_pose[16], pf_track_stats* stats_host, void* stream)
 {
     return pf::keep_status(v, pf_track_frame_impl(v, depth_dev, intr, p, init_pose, out_pose, stats_host, stream));
 }
 
-pf_status pf_fitness_noalloc(const pf_volume* v, const float* points_dev, int n, const float* poses_dev, int k, float* fitness_dev, int* count_dev, void* stream)
+pf_status pf_fitness_noalloc(const pf_volume* v, const float* points_dev, int n, const float* poses_dev, int k,
+                             float* fitness_dev, int* count_dev, void* stream)
 {
-    return pf::keep_status(v, pf_fitness_noalloc_impl(v, points_dev, n, poses_dev, k, fitness_dev, count_dev, stream));
+    return pf::keep_status(v, pf_fitness_noalloc_impl(v, points_dev, n, poses_dev, k, fitness_dev, count_dev,
+                                                      stream));
 }
 
 }  // extern "C"

@@ -735,15 +735,15 @@ __global__ void compose_kernel(const double* A, const double* B, double* out)
 
 extern "C" {
 
-static pf_status pf_integrate_impl(pf_volume* v, const float* depth_dev, const pf_intrinsics* intr, const double P[16],
-                       void* stream)
+static pf_status pf_integrate_impl(pf_volume* v, const float* depth_dev, const pf_intrinsics* intr,
+                                   const double P[16], void* stream)
 {
     if (!P || !finite_pose(P)) return PF_ERR_INVALID_ARG;
     return integrate_impl(v, depth_dev, intr, P, nullptr, (cudaStream_t)stream);
 }
 
 static pf_status pf_integrate_async_impl(pf_volume* v, const float* depth_dev, const pf_intrinsics* intr,
-                             const double* P_dev, void* stream)
+                                         const double* P_dev, void* stream)
 {
     if (!P_dev) return PF_ERR_INVALID_ARG;
     return integrate_impl(v, depth_dev, intr, nullptr, P_dev, (cudaStream_t)stream);
@@ -792,12 +792,14 @@ pf_status pf_volume_download(const pf_volume* v, float* tsdf_host, float* weight
     return pf::keep_status(v, pf_volume_download_impl(v, tsdf_host, weight_host));
 }
 
-pf_status pf_integrate(pf_volume* v, const float* depth_dev, const pf_intrinsics* intr, const double P[16], void* stream)
+pf_status pf_integrate(pf_volume* v, const float* depth_dev, const pf_intrinsics* intr, const double P[16],
+                       void* stream)
 {
     return pf::keep_status(v, pf_integrate_impl(v, depth_dev, intr, P, stream));
 }
 
-pf_status pf_integrate_async(pf_volume* v, const float* depth_dev, const pf_intrinsics* intr, const double* P_dev, void* stream)
+pf_status pf_integrate_async(pf_volume* v, const float* depth_dev, const pf_intrinsics* intr, const double* P_dev,
+                             void* stream)
 {
     return pf::keep_status(v, pf_integrate_async_impl(v, depth_dev, intr, P_dev, stream));
 }
