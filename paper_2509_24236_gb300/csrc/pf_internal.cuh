@@ -121,6 +121,11 @@ struct pf_workspace {
     float* part_S = nullptr;         // part_cap
     int* part_C = nullptr;           // part_cap
     unsigned int* counter = nullptr; // last-block tickets (zeroed, reset by the last block)
+    void* chunks = nullptr;          // the particle chunks of a search iteration, see track.cu
+    int chunk_cap = 0;               // chunks it holds
+    unsigned int* chunk_counter = nullptr;  // per chunk: tickets of its point tiles (zeroed, reset by the last)
+    float* chunk_E = nullptr;        // per particle: fitness of the search iteration (chunk_cap x 32)
+    int* chunk_C = nullptr;          // per particle: valid points
     double* state = nullptr;         // search state, see track.cu
     double* pose_in = nullptr;       // 16 (sync entry point)
     double* pose_out = nullptr;      // 16

@@ -217,6 +217,13 @@ struct FitArgs {
     const float* poses;   // SRC_POSES: K x 12
     float pm_threshold;   // particles on lanes when the chunk's spread (voxels) is below this
     const float* templ;   // SRC_SEARCH: templates, row k = particle k
+    const void* chunks;   // the launch's particle chunks built by chunk_build_kernel, or null: each CTA builds its own
+    // search, two-level reduction (or null: the launch's last CTA reduces
+    // every particle over the point tiles): the last CTA of each chunk writes
+    // its particles' E and count here, the last chunk to finish selects
+    unsigned int* chunk_counter;
+    float* chunk_E;
+    int* chunk_C;
     SearchState* st;
     int compose_mode, update_mode;
     double beta;
@@ -771,16 +778,100 @@ __device__ __forceinline__ void sum_tiles(const float* part_S, const int* part_C
     }
 }
 
+// A particle chunk as a fitness CTA uses it: the chunk's particles in both
+// forms, its reference matrix as a float pair, and the chunk's spread and
+// reach (see fitness_body).  chunk_build_kernel forms it once per search
+// iteration, one warp per chunk, so the CTAs of the chunk's point tiles copy
+// it instead of each repeating the FP64 construction of 32 particles (~20 us
+// per CTA, measured) and the serial reach loop.
+struct ChunkData {
+    Particle P[KC];
+    ParticleD PD[KC];
+    float ref[18];
+    float spread[2];   // largest translation (voxels) and rotation (voxels per metre) against particle 0
+    float dmax;        // largest row sum of |dA_k| (infinite when some particle is not finite)
+    int omin[3], omax[3];
+    int pad;
+};
+static_assert(sizeof(ChunkData) % 16 == 0, "ChunkData is copied as 16-byte words");
+
+// One warp per chunk: thread t builds particle k_begin + t exactly as a CTA
+// would (build_particles, make_particle_d), and the chunk's spread and reach
+// come from warp reductions of the per-particle values (maxima and minima:
+// the same values as the serial loop, whatever the order).
+template <int SRC>
+__global__ void __launch_bounds__(32) chunk_build_kernel(FitArgs a, ChunkData* out)
+{
+    const int t = threadIdx.x;
+    const int k_begin = blockIdx.x * KC;
+    const int kc = min(KC, a.K - k_begin);
+    if (SRC != SRC_POSES && a.st->lost) return;  // the fitness launch skips every chunk then
+    ChunkData& C = out[blockIdx.x];
+    const int nx = a.nx, nxy = a.nx * a.ny;
+    build_particles<SRC>(a, k_begin, kc, C.P, C.ref, nullptr);
+    __syncwarp();
+    const bool mine = t < kc;
+    Particle P;
+    if (mine) {
+        P = C.P[t];
+        make_particle_d(P, nx, nxy, C.PD[t]);
+    }
+    const float4 row[3] = {mine ? P.d0 : make_float4(0, 0, 0, 0), mine ? P.d1 : make_float4(0, 0, 0, 0),
+                           mine ? P.d2 : make_float4(0, 0, 0, 0)};
+    const int m[3] = {mine ? P.m.x : 0, mine ? P.m.y : 0, mine ? P.m.z : 0};
+    float dt = 0.0f, dr = 0.0f, dmax = 0.0f;
+    int omin[3], omax[3];
+    for (int r = 0; r < 3; ++r) {
+        // particle 0 of the chunk, as the serial loop takes it
+        const float o0 = (float)(kMagicBits - __shfl_sync(0xffffffffu, m[r], 0));
+        const float b0 = __shfl_sync(0xffffffffu, row[r].w, 0);
+        const int o = kMagicBits - m[r];
+        omin[r] = mine ? o : INT_MAX;
+        omax[r] = mine ? o : INT_MIN;
+        if (mine) {
+            const float sum = fabsf(row[r].x) + fabsf(row[r].y) + fabsf(row[r].z);
+            dmax = (sum < INFINITY && fabsf(row[r].w) <= 1.0f) ? fmaxf(dmax, sum) : INFINITY;
+            if (t > 0) {
+                dt = fmaxf(dt, fabsf((float)(kMagicBits - m[r]) + row[r].w - (o0 + b0)));
+                dr = fmaxf(dr, sum);
+            }
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        dt = fmaxf(dt, __shfl_xor_sync(0xffffffffu, dt, o));
+        dr = fmaxf(dr, __shfl_xor_sync(0xffffffffu, dr, o));
+        dmax = fmaxf(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
+    }
+    for (int r = 0; r < 3; ++r) {
+        omin[r] = __reduce_min_sync(0xffffffffu, omin[r]);
+        omax[r] = __reduce_max_sync(0xffffffffu, omax[r]);
+    }
+    if (t == 0) {
+        C.spread[0] = dt;
+        C.spread[1] = dr;
+        C.dmax = dmax;
+        for (int r = 0; r < 3; ++r) {
+            C.omin[r] = omin[r];
+            C.omax[r] = omax[r];
+        }
+        C.pad = 0;
+    }
+}
+
 // The work of one CTA: particle chunk bx, point tile by, of a launch of
 // n_blocks CTAs for this problem (the last of them to finish runs the
 // epilogue).
-template <int SRC, int VARIANT, typename TS>
+// SOLO: a launch of one problem, which may use prebuilt particle chunks and
+// the two-level reduction (FitArgs.chunks, .chunk_counter); the batched
+// launch compiles without them.
+template <int SRC, int VARIANT, typename TS, bool SOLO>
 __device__ __forceinline__ void fitness_body(const FitArgs& a, int bx, int by, unsigned n_blocks)
 {
-    __shared__ Particle sP[KC];
-    __shared__ ParticleD sPD[KC];
+    __shared__ __align__(16) ChunkData sC;
+    Particle* const sP = sC.P;
+    ParticleD* const sPD = sC.PD;
+    float* const sRef = sC.ref;
     __shared__ PlainXf sAbs[VARIANT == 1 ? KC : 1];
-    __shared__ float sRef[18];
     // particles on lanes: each warp's points as pairs (point q, point q + 64
     // of the warp): (x, y), (z, yf0), (yf1, yf2), and their reference cells
     __shared__ float4 sPair[FIT_WARPS][PPT * 16][3];
@@ -790,9 +881,9 @@ __device__ __forceinline__ void fitness_body(const FitArgs& a, int bx, int by, u
     __shared__ int s_last;
     __shared__ int s_skip;
     __shared__ int s_mode;
-    __shared__ float s_spread[2];
+    float* const s_spread = sC.spread;
     __shared__ float s_red[FIT_WARPS];
-    __shared__ float s_dmax;
+    float& s_dmax = sC.dmax;
     __shared__ long long s_omin[3], s_omax[3];
     __shared__ int s_lo[3], s_hi[3];
 
@@ -816,17 +907,30 @@ __device__ __forceinline__ void fitness_body(const FitArgs& a, int bx, int by, u
     }
     __syncthreads();
     const bool skip = s_skip != 0;
+    const bool prebuilt = SOLO && SRC == SRC_SEARCH && a.chunks != nullptr;  // (never with the plain layout)
     if (!skip) {
-        build_particles<SRC>(a, k_begin, kc, sP, sRef, VARIANT == 1 ? sAbs : nullptr);
-        if (tid < kc) make_particle_d(sP[tid], nx, nxy, sPD[tid]);
+        if (prebuilt) {
+            const int4* src = reinterpret_cast<const int4*>(static_cast<const ChunkData*>(a.chunks) + bx);
+            int4* dst = reinterpret_cast<int4*>(&sC);
+            for (int q = tid; q < (int)(sizeof(ChunkData) / 16); q += FIT_THREADS) dst[q] = __ldg(src + q);
+        } else {
+            build_particles<SRC>(a, k_begin, kc, sP, sRef, VARIANT == 1 ? sAbs : nullptr);
+            if (tid < kc) make_particle_d(sP[tid], nx, nxy, sPD[tid]);
+        }
     }
     __syncthreads();
+    if (prebuilt && tid == 0) {
+        for (int r = 0; r < 3; ++r) {
+            s_omin[r] = skip ? LLONG_MAX : (long long)sC.omin[r];
+            s_omax[r] = skip ? LLONG_MIN : (long long)sC.omax[r];
+        }
+    }
     // spread of the chunk's particles relative to its first one: translation
     // (voxels) and rotation (voxels per metre of point distance); and the
     // chunk's reach: the range of the particles' integer cell offsets o_k
     // and the largest row sum of |dA_k|, which bound where any particle can
     // put a point (see the interior test below)
-    if (tid == 0) {
+    if (!prebuilt && tid == 0) {
         float dt = 0.0f, dr = 0.0f, dmax = 0.0f;
         long long omin[3] = {LLONG_MAX, LLONG_MAX, LLONG_MAX}, omax[3] = {LLONG_MIN, LLONG_MIN, LLONG_MIN};
         if (!skip) {
@@ -1128,9 +1232,37 @@ __device__ __forceinline__ void fitness_body(const FitArgs& a, int bx, int by, u
     }
     __threadfence();
     __syncthreads();
-    if (tid == 0) {
-        const unsigned int ticket = atomicAdd(a.counter, 1u);
-        s_last = ticket == n_blocks - 1;
+    const bool two_level = SOLO && SRC == SRC_SEARCH && a.chunk_counter != nullptr;
+    if (two_level) {
+        // the last of the chunk's point tiles reduces the chunk's particles
+        // over the tiles (in parallel with other chunks' sampling) ...
+        if (tid == 0) {
+            const unsigned int ticket = atomicAdd(a.chunk_counter + bx, 1u);
+            s_last = ticket == (unsigned)a.n_ptiles - 1;
+        }
+        __syncthreads();
+        if (!s_last) return;
+        __threadfence();
+        if (tid < kc) {
+            float S;
+            int C;
+            sum_tiles(a.part_S, a.part_C, a.K, a.n_ptiles, k_begin + tid, S, C);
+            a.chunk_E[k_begin + tid] = C > 0 ? __fdiv_rn(S, (float)C) : INFINITY;
+            a.chunk_C[k_begin + tid] = C;
+        }
+        if (tid == 0) a.chunk_counter[bx] = 0u;
+        __threadfence();
+        __syncthreads();
+        // ... and the last chunk to finish runs the selection below
+        if (tid == 0) {
+            const unsigned int ticket = atomicAdd(a.counter, 1u);
+            s_last = ticket == (unsigned)((a.K + KC - 1) / KC) - 1;
+        }
+    } else {
+        if (tid == 0) {
+            const unsigned int ticket = atomicAdd(a.counter, 1u);
+            s_last = ticket == n_blocks - 1;
+        }
     }
     __syncthreads();
     if (!s_last) return;
@@ -1192,11 +1324,16 @@ __device__ __forceinline__ void fitness_body(const FitArgs& a, int bx, int by, u
         __shared__ int sn[FIT_WARPS];
         SearchState* st = a.st;
         if (tid == 0) {
-            float S;
-            int C;
-            sum_tiles(a.part_S, a.part_C, a.K, a.n_ptiles, 0, S, C);
-            s_E0 = C > 0 ? __fdiv_rn(S, (float)C) : INFINITY;
-            s_C0 = C;
+            if (two_level) {
+                s_E0 = __ldcg(a.chunk_E);
+                s_C0 = __ldcg(a.chunk_C);
+            } else {
+                float S;
+                int C;
+                sum_tiles(a.part_S, a.part_C, a.K, a.n_ptiles, 0, S, C);
+                s_E0 = C > 0 ? __fdiv_rn(S, (float)C) : INFINITY;
+                s_C0 = C;
+            }
         }
         __syncthreads();
         const float E0 = s_E0;
@@ -1205,10 +1342,15 @@ __device__ __forceinline__ void fitness_body(const FitArgs& a, int bx, int by, u
         int nadv = 0;
         double sum[6] = {0, 0, 0, 0, 0, 0};
         for (int k = tid; k < a.K; k += FIT_THREADS) {
-            float S;
-            int C;
-            sum_tiles(a.part_S, a.part_C, a.K, a.n_ptiles, k, S, C);
-            const float E = C > 0 ? __fdiv_rn(S, (float)C) : INFINITY;
+            float E;
+            if (two_level) {
+                E = __ldcg(a.chunk_E + k);
+            } else {
+                float S;
+                int C;
+                sum_tiles(a.part_S, a.part_C, a.K, a.n_ptiles, k, S, C);
+                E = C > 0 ? __fdiv_rn(S, (float)C) : INFINITY;
+            }
             if (E < be) {
                 be = E;
                 bk = k;
@@ -1303,7 +1445,7 @@ __device__ __forceinline__ void fitness_body(const FitArgs& a, int bx, int by, u
 template <int SRC, int VARIANT, typename TS>
 __global__ void __launch_bounds__(FIT_THREADS, PF_FIT_MIN_BLOCKS) fitness_kernel(FitArgs a)
 {
-    fitness_body<SRC, VARIANT, TS>(a, blockIdx.x, blockIdx.y, gridDim.x * gridDim.y);
+    fitness_body<SRC, VARIANT, TS, true>(a, blockIdx.x, blockIdx.y, gridDim.x * gridDim.y);
 }
 
 // One launch over the CTAs of several independent problems (the sequences
@@ -1336,7 +1478,7 @@ __global__ void __launch_bounds__(FIT_THREADS, PF_FIT_MIN_BLOCKS)
     __syncthreads();
     const int local = (int)blockIdx.x - __ldg(first + id);
     const int chunks = (sa.K + KC - 1) / KC;
-    fitness_body<SRC, VARIANT, TS>(sa, local % chunks, local / chunks, (unsigned)(chunks * sa.n_ptiles));
+    fitness_body<SRC, VARIANT, TS, false>(sa, local % chunks, local / chunks, (unsigned)(chunks * sa.n_ptiles));
 }
 
 __global__ void track_begin_kernel(SearchState* st, const double* P0, double s_deg, double s_cm,
@@ -1424,6 +1566,13 @@ void launch_fitness_t(const FitArgs& a, int layout, dim3 grid, cudaStream_t s)
         fitness_kernel<SRC, 0, TS><<<grid, FIT_THREADS, 0, s>>>(a);
     else
         fitness_kernel<SRC, 2, TS><<<grid, FIT_THREADS, 0, s>>>(a);
+}
+
+// Layout the fitness of this volume runs with (see pf_set_fitness_variant).
+int resolve_fitness_layout(const pf_volume* v)
+{
+    const int layout = v->fitness_variant & 3;
+    return layout == 0 ? (v->cells ? 3 : 2) : layout;
 }
 
 template <int SRC>
@@ -1521,6 +1670,25 @@ pf_status workspace_reserve(pf_volume* v, int max_pixels, int k_max)
     }
     pf_status st = grow_partials(v, need);
     if (st != PF_OK) return st;
+    const int chunks_needed = (k_max + KC - 1) / KC;
+    if (w.chunk_cap < chunks_needed) {
+        PF_CUDA(cudaDeviceSynchronize());
+        cudaFree(w.chunks);
+        w.chunks = nullptr;
+        w.chunk_cap = 0;
+        cudaFree(w.chunk_counter);
+        cudaFree(w.chunk_E);
+        cudaFree(w.chunk_C);
+        w.chunk_counter = nullptr;
+        w.chunk_E = nullptr;
+        w.chunk_C = nullptr;
+        PF_CUDA(pf::dev_malloc(reinterpret_cast<ChunkData**>(&w.chunks), sizeof(ChunkData) * (size_t)chunks_needed));
+        PF_CUDA(pf::dev_malloc(&w.chunk_counter, sizeof(unsigned int) * (size_t)chunks_needed));
+        PF_CUDA(cudaMemset(w.chunk_counter, 0, sizeof(unsigned int) * (size_t)chunks_needed));
+        PF_CUDA(pf::dev_malloc(&w.chunk_E, sizeof(float) * KC * (size_t)chunks_needed));
+        PF_CUDA(pf::dev_malloc(&w.chunk_C, sizeof(int) * KC * (size_t)chunks_needed));
+        w.chunk_cap = chunks_needed;
+    }
     if (w.pix_cap < max_pixels) {
         PF_CUDA(cudaDeviceSynchronize());
         cudaFree(w.points);
@@ -1653,12 +1821,27 @@ static pf_status pf_track_frame_async_impl(pf_volume* v, const float* depth_dev,
         a.stride = stride;
         a.iter = it;
         a.n_ptiles = choose_ptiles(v->device, chunks, ne_max);
-        if ((size_t)a.n_ptiles * K > (size_t)w.part_cap) return PF_ERR_INVALID_ARG;
+        if ((size_t)a.n_ptiles * K > (size_t)w.part_cap || chunks > w.chunk_cap) return PF_ERR_INVALID_ARG;
+        // the iteration's particles, built once (the plain baseline layout
+        // builds its own in every CTA, as it always did)
+        const bool prebuild = resolve_fitness_layout(v) != 1;
+        a.chunks = prebuild ? w.chunks : nullptr;
+        a.chunk_counter = w.chunk_counter;
+        a.chunk_E = w.chunk_E;
+        a.chunk_C = w.chunk_C;
         pf::timing_begin(pf::KC_FITNESS, s);
+        if (prebuild) {
+            chunk_build_kernel<SRC_SEARCH><<<chunks, 32, 0, s>>>(a, static_cast<ChunkData*>(w.chunks));
+            pf::count_launch();
+        }
         launch_fitness<SRC_SEARCH>(a, v->fitness_variant, v, chunks, s);
         pf::timing_end(pf::KC_FITNESS, s);
         if (p->update_mode == 0) {
             FitArgs e = a;
+            e.chunks = nullptr;  // one particle, built in its CTAs, reduced by the launch's last CTA
+            e.chunk_counter = nullptr;
+            e.chunk_E = nullptr;
+            e.chunk_C = nullptr;
             e.K = 1;
             e.n_ptiles = choose_ptiles(v->device, 1, ne_max);
             pf::timing_begin(pf::KC_FITNESS1, s);
@@ -1753,11 +1936,7 @@ struct pf_batch {
 
 namespace {
 
-int resolve_layout(const pf_volume* v)
-{
-    const int layout = v->fitness_variant & 3;
-    return layout == 0 ? (v->cells ? 3 : 2) : layout;
-}
+int resolve_layout(const pf_volume* v) { return resolve_fitness_layout(v); }
 
 float mapping_threshold(const pf_volume* v, int layout)
 {

@@ -544,6 +544,10 @@ pf_status pf_destroy_volume(pf_volume* v)
     cudaFree(w.n_points);
     cudaFree(w.part_S);
     cudaFree(w.part_C);
+    cudaFree(w.chunks);
+    cudaFree(w.chunk_counter);
+    cudaFree(w.chunk_E);
+    cudaFree(w.chunk_C);
     cudaFree(w.counter);
     cudaFree(w.state);
     cudaFree(w.pose_in);
