@@ -126,6 +126,13 @@ struct pf_workspace {
     unsigned int* chunk_counter = nullptr;  // per chunk: tickets of its point tiles (zeroed, reset by the last)
     float* chunk_E = nullptr;        // per particle: fitness of the search iteration (chunk_cap x 32)
     int* chunk_C = nullptr;          // per particle: valid points
+    // decimated point sets in a locality order (see track.cu): each point's
+    // tile, the reordered kept points of up to three strides, counters
+    int* point_tile = nullptr;       // pix_cap
+    float4* kept = nullptr;          // 2 x pix_cap
+    int* kept_count = nullptr;       // 3: kept points of each stride
+    int* order_scratch = nullptr;    // order_cap: per (block of tiles, tile row) counts and first indices, offsets
+    int order_cap = 0;
     double* state = nullptr;         // search state, see track.cu
     double* pose_in = nullptr;       // 16 (sync entry point)
     double* pose_out = nullptr;      // 16

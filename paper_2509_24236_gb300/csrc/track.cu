@@ -134,7 +134,7 @@ __global__ void __launch_bounds__(BP_THREADS) bp_count_kernel(const float* __res
 
 __global__ void __launch_bounds__(BP_THREADS) bp_write_kernel(const float* __restrict__ depth, CamK cam, int n_tiles,
                                                               int tiles_x, const int* __restrict__ block_counts,
-                                                              float4* __restrict__ pts, int* n_out)
+                                                              float4* __restrict__ pts, int* n_out, int* tile_out)
 {
     __shared__ int sh[32];
     __shared__ int warp_off[BP_THREADS / 32];
@@ -168,6 +168,7 @@ __global__ void __launch_bounds__(BP_THREADS) bp_write_kernel(const float* __res
             const float x = __fdiv_rn(((float)u - cam.cx) * z, cam.fx);
             const float y = __fdiv_rn(((float)v - cam.cy) * z, cam.fy);
             pts[pos + __popc(m & below)] = make_float4(x, y, z, 0.0f);
+            if (tile_out) tile_out[pos + __popc(m & below)] = tile;
         }
         pos += __popc(m);
     }
@@ -175,7 +176,7 @@ __global__ void __launch_bounds__(BP_THREADS) bp_write_kernel(const float* __res
 }
 
 pf_status enqueue_backproject(const float* depth, const pf_intrinsics* intr, float4* pts, int* block_counts,
-                              int* n_out, cudaStream_t s)
+                              int* n_out, cudaStream_t s, int* tile_out = nullptr)
 {
     const int tiles_x = (intr->width + TILE_W - 1) / TILE_W, tiles_y = (intr->height + TILE_H - 1) / TILE_H;
     const int n_tiles = tiles_x * tiles_y;
@@ -183,11 +184,124 @@ pf_status enqueue_backproject(const float* depth, const pf_intrinsics* intr, flo
     CamK cam = make_cam(intr);
     pf::timing_begin(pf::KC_BACKPROJECT, s);
     bp_count_kernel<<<blocks, BP_THREADS, 0, s>>>(depth, cam, n_tiles, tiles_x, block_counts);
-    bp_write_kernel<<<blocks, BP_THREADS, 0, s>>>(depth, cam, n_tiles, tiles_x, block_counts, pts, n_out);
+    bp_write_kernel<<<blocks, BP_THREADS, 0, s>>>(depth, cam, n_tiles, tiles_x, block_counts, pts, n_out, tile_out);
     pf::count_launch(2);
     pf::timing_end(pf::KC_BACKPROJECT, s);
     PF_LAUNCHED();
     return PF_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Decimated point sets in a locality order.
+//
+// Down-sampling by n keeps the compacted points j = 0, n, 2n, ... (tile
+// order).  Taken in that order, the 32 points a warp evaluates together lie
+// up to 32 image tiles apart, so under one particle they share no cells and
+// each warp-wide record load touches ~32 sectors.  The kept points are
+// therefore evaluated in another order: grouped by blocks of SC x SR image
+// tiles (about n tiles, ~32 kept points), blocks row-major, and within a block
+// by tile row, keeping the order of the kept sequence inside each row.  The
+// order is a function of the input alone (counts, minima and a scan: no
+// order-dependent atomics), and the set of points is the kept set, so only
+// the float summation order of the fitness changes.
+// ---------------------------------------------------------------------------
+// Strides above this keep the strided reading (their blocks would be large
+// and their points sparse anyway).
+constexpr int kMaxOrderedStride = 64;
+
+// Scratch slots the ordering needs for an image of `pixels` pixels and any
+// stride up to kMaxOrderedStride (blocks x rows <= tiles + tiles_x x rows).
+inline size_t kept_slots_bound(size_t pixels) { return pixels / 32 + 2 * 2048 + 4096 + 2048 * 8 + 64; }
+
+struct KeptOrder {
+    int stride;          // n > 1
+    int tiles_x, sc, sr; // image tiles per row; block of sc x sr tiles
+    int blocks_x;        // blocks per row of blocks
+    int n_slots;         // blocks x sr
+};
+
+inline KeptOrder kept_order(int stride, int width, int height)
+{
+    KeptOrder o;
+    o.stride = stride;
+    o.tiles_x = (width + TILE_W - 1) / TILE_W;
+    const int tiles_y = (height + TILE_H - 1) / TILE_H;
+    o.sc = std::max(1, (int)std::ceil(std::sqrt((double)stride)));
+    o.sr = std::max(1, (stride + o.sc - 1) / o.sc);
+    o.blocks_x = (o.tiles_x + o.sc - 1) / o.sc;
+    const int blocks_y = (tiles_y + o.sr - 1) / o.sr;
+    o.n_slots = o.blocks_x * blocks_y * o.sr;
+    return o;
+}
+
+__device__ __forceinline__ void kept_slot(const KeptOrder& o, int tile, int& block, int& row)
+{
+    const int tx = tile % o.tiles_x, ty = tile / o.tiles_x;
+    block = (ty / o.sr) * o.blocks_x + tx / o.sc;
+    row = ty % o.sr;
+}
+
+__global__ void kept_clear_kernel(int* cnt, int* first, int n_slots)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n_slots; i += gridDim.x * blockDim.x) {
+        cnt[i] = 0;
+        first[i] = INT_MAX;
+    }
+}
+
+// per (block, tile row): how many kept points, and the first of them
+__global__ void kept_count_kernel(KeptOrder o, const int* n_points, const int* point_tile, int* cnt, int* first)
+{
+    const int N = *n_points;
+    const int ne = (N + o.stride - 1) / o.stride;
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < ne; e += gridDim.x * blockDim.x) {
+        int block, row;
+        kept_slot(o, point_tile[(size_t)e * o.stride], block, row);
+        atomicAdd(cnt + block * o.sr + row, 1);
+        atomicMin(first + block * o.sr + row, e);
+    }
+}
+
+// exclusive scan of the per-slot counts in slot order (one block)
+__global__ void __launch_bounds__(256) kept_scan_kernel(const int* cnt, int* offset, int n_slots)
+{
+    __shared__ int s_part[256];
+    const int per = (n_slots + 255) / 256;
+    const int beg = min(n_slots, (int)threadIdx.x * per), end = min(n_slots, beg + per);
+    int sum = 0;
+    for (int i = beg; i < end; ++i) sum += cnt[i];
+    s_part[threadIdx.x] = sum;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int acc = 0;
+        for (int t = 0; t < 256; ++t) {
+            const int v = s_part[t];
+            s_part[t] = acc;
+            acc += v;
+        }
+    }
+    __syncthreads();
+    int acc = s_part[threadIdx.x];
+    for (int i = beg; i < end; ++i) {
+        offset[i] = acc;
+        acc += cnt[i];
+    }
+}
+
+__global__ void kept_write_kernel(KeptOrder o, const int* n_points, const float4* __restrict__ pts,
+                                  const int* point_tile, const int* first, const int* offset, float4* kept,
+                                  int* kept_count)
+{
+    const int N = *n_points;
+    const int ne = (N + o.stride - 1) / o.stride;
+    if (blockIdx.x == 0 && threadIdx.x == 0) *kept_count = ne;
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < ne; e += gridDim.x * blockDim.x) {
+        int block, row;
+        const size_t j = (size_t)e * o.stride;
+        kept_slot(o, point_tile[j], block, row);
+        const int slot = block * o.sr + row;
+        kept[offset[slot] + (e - first[slot])] = pts[j];
+    }
 }
 
 // number of back-projection blocks for a w x h image
@@ -1693,9 +1807,24 @@ pf_status workspace_reserve(pf_volume* v, int max_pixels, int k_max)
         PF_CUDA(cudaDeviceSynchronize());
         cudaFree(w.points);
         cudaFree(w.block_counts);
+        cudaFree(w.point_tile);
+        cudaFree(w.kept);
+        cudaFree(w.kept_count);
+        cudaFree(w.order_scratch);
         w.points = nullptr;
         w.block_counts = nullptr;
+        w.point_tile = nullptr;
+        w.kept = nullptr;
+        w.kept_count = nullptr;
+        w.order_scratch = nullptr;
+        w.order_cap = 0;
         w.pix_cap = 0;
+        PF_CUDA(pf::dev_malloc(&w.point_tile, sizeof(int) * (size_t)max_pixels));
+        PF_CUDA(pf::dev_malloc(&w.kept, 2 * sizeof(float4) * (size_t)max_pixels));
+        PF_CUDA(pf::dev_malloc(&w.kept_count, 4 * sizeof(int)));
+        const size_t slots = kept_slots_bound((size_t)max_pixels);
+        PF_CUDA(pf::dev_malloc(&w.order_scratch, 3 * sizeof(int) * slots));
+        w.order_cap = (int)slots;
         PF_CUDA(pf::dev_malloc(&w.points, sizeof(float4) * (size_t)max_pixels));
         // one count per back-projection block: an image of max_pixels pixels has
         // at most max_pixels tiles (thin images leave tiles partly empty)
@@ -1794,8 +1923,39 @@ static pf_status pf_track_frame_async_impl(pf_volume* v, const float* depth_dev,
 
     track_begin_kernel<<<1, 32, 0, s>>>(state, init_pose_dev, p->init_rot_deg, p->init_trans_cm, stats);
     pf::count_launch();
-    st = enqueue_backproject(depth_dev, intr, w.points, w.block_counts, w.n_points, s);
+    st = enqueue_backproject(depth_dev, intr, w.points, w.block_counts, w.n_points, s, w.point_tile);
     if (st != PF_OK) return st;
+    // the decimated point sets of the schedule, each in a locality order
+    int kept_stride[3] = {0, 0, 0};
+    const float4* kept_pts[3] = {nullptr, nullptr, nullptr};
+    int n_kept = 0;
+    size_t kept_off = 0;
+    for (int i = 0; i < 3; ++i) {
+        const int n = p->decim_sched[i];
+        bool seen = false;
+        for (int d = 0; d < n_kept; ++d) seen = seen || kept_stride[d] == n;
+        if (n <= 1 || n > kMaxOrderedStride || seen) continue;
+        const KeptOrder o = kept_order(n, intr->width, intr->height);
+        if (o.n_slots > w.order_cap) continue;  // (cannot happen within the bound; strided reading then)
+        int* cnt = w.order_scratch;
+        int* first = cnt + w.order_cap;
+        int* offset = first + w.order_cap;
+        const int ne_max = (npix + n - 1) / n;
+        const int grid = std::max(1, std::min(1024, (ne_max + 255) / 256));
+        pf::timing_begin(pf::KC_BACKPROJECT, s);
+        kept_clear_kernel<<<std::max(1, std::min(1024, (o.n_slots + 255) / 256)), 256, 0, s>>>(cnt, first, o.n_slots);
+        kept_count_kernel<<<grid, 256, 0, s>>>(o, w.n_points, w.point_tile, cnt, first);
+        kept_scan_kernel<<<1, 256, 0, s>>>(cnt, offset, o.n_slots);
+        kept_write_kernel<<<grid, 256, 0, s>>>(o, w.n_points, w.points, w.point_tile, first, offset,
+                                               w.kept + kept_off, w.kept_count + n_kept);
+        pf::count_launch(4);
+        pf::timing_end(pf::KC_BACKPROJECT, s);
+        PF_LAUNCHED();
+        kept_stride[n_kept] = n;
+        kept_pts[n_kept] = w.kept + kept_off;
+        kept_off += (size_t)ne_max;
+        ++n_kept;
+    }
 
     FitArgs a;
     memset(&a, 0, sizeof(a));
@@ -1818,7 +1978,15 @@ static pf_status pf_track_frame_async_impl(pf_volume* v, const float* depth_dev,
         const long long ne_max = ((long long)npix + stride - 1) / stride;
         const int chunks = (K + KC - 1) / KC;
         a.K = K;
+        a.pts = w.points;
+        a.n_dev = w.n_points;
         a.stride = stride;
+        for (int d = 0; d < n_kept; ++d)
+            if (kept_stride[d] == stride) {  // the kept points, already in their locality order
+                a.pts = kept_pts[d];
+                a.n_dev = w.kept_count + d;
+                a.stride = 1;
+            }
         a.iter = it;
         a.n_ptiles = choose_ptiles(v->device, chunks, ne_max);
         if ((size_t)a.n_ptiles * K > (size_t)w.part_cap || chunks > w.chunk_cap) return PF_ERR_INVALID_ARG;

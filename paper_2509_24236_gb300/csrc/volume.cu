@@ -545,6 +545,10 @@ pf_status pf_destroy_volume(pf_volume* v)
     cudaFree(w.part_S);
     cudaFree(w.part_C);
     cudaFree(w.chunks);
+    cudaFree(w.point_tile);
+    cudaFree(w.kept);
+    cudaFree(w.kept_count);
+    cudaFree(w.order_scratch);
     cudaFree(w.chunk_counter);
     cudaFree(w.chunk_E);
     cudaFree(w.chunk_C);

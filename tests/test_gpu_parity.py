@@ -361,6 +361,8 @@ def test_track_decimated_schedule(pf):
     assert list(st["k_used"]) == list(ores.stats["k_used"])
     assert list(st["n_eval"]) == list(ores.stats["n_eval"])
     assert st["best"][0] == ores.stats["best"][0]
+    assert st["n_valid0"][0] == ores.stats["n_valid0"][0]
+    assert abs(st["E0"][0] - ores.stats["E0"][0]) <= 1e-5 * ores.stats["E0"][0]
     assert pose_trans_err(pose, ores.pose) <= 1e-4 and pose_rot_err(pose, ores.pose) <= 1e-4
 
 
@@ -387,6 +389,10 @@ def test_track_paper_schedule_with_10240_particles(pf):
         if not (os_["best_gap"][i] > 3e-5 and os_["adv_margin"][i] > 3e-5):
             break
         assert st["best"][i] == os_["best"][i] and st["n_adv"][i] == os_["n_adv"][i], i
+        # the kept points are evaluated in a locality order (the same set):
+        # the fitness of the entering pose still matches
+        assert abs(st["E0"][i] - os_["E0"][i]) <= 1e-5 * os_["E0"][i], i
+        assert st["n_valid0"][i] == os_["n_valid0"][i], i
     assert pose_trans_err(pose, ores.pose) <= 1e-4 and pose_rot_err(pose, ores.pose) <= 1e-4
 
 
