@@ -342,6 +342,47 @@ def test_track_lost_on_empty_frame(pf):
     assert status == pf.PF_ERR_TRACK_LOST
     assert np.array_equal(pose, fr.init_pose)
     assert st["n_points"] == 0 and st["status"] == pf.PF_ERR_TRACK_LOST
+    # the same with a decimated schedule: no point is kept at any stride
+    params = pf.track_params(tdev, n_iters=3, k_sched=(64, 64, 64), decim_sched=(8, 16, 32))
+    status, pose, st = vol.track_frame(to_dev(np.zeros_like(fr.depth)), synth.ROOM64_INTR, params, fr.init_pose)
+    assert status == pf.PF_ERR_TRACK_LOST and np.array_equal(pose, fr.init_pose)
+    assert st["n_points"] == 0 and st["status"] == pf.PF_ERR_TRACK_LOST
+
+
+def test_track_decimated_schedule_on_a_ragged_image(pf):
+    """Strides 3 / 7 / 13 on a 173 x 97 image (partial tiles on both edges,
+    blocks of tiles cut by the image border): the kept points, evaluated in
+    their locality order, give the oracle's counts, E0, best index and pose."""
+    torch = torch_cuda()
+    scene = synth.room_scene(1)
+    tsdf, weight = synth.analytic_tsdf(scene, synth.ROOM64_GRID, hole_bricks=0.0, seed=1)
+    vol = pf.Volume.from_grid(synth.ROOM64_GRID)
+    vol.upload(tsdf, weight)
+    ovol = oracle.Volume(abi(synth.ROOM64_GRID), tsdf, weight)
+    intr = Intrinsics(173, 97, 150.0, 148.0, 86.2, 48.7, 0.1, 8.0)
+    gt = synth.room_view(scene, 1)
+    depth = synth.render_depth(scene, intr, gt)
+    init = gt @ synth.perturbation(41, 0, 3.0, 3.0)
+    templ = synth.templates(1024, 3)
+    ks, ds = (256, 512, 1024), (3, 7, 13)
+    params = pf.track_params(torch.from_numpy(templ).cuda(), n_iters=6, k_sched=ks, decim_sched=ds,
+                             update_mode=1, compose_mode=1)
+    status, pose, st = vol.track_frame(to_dev(depth), intr, params, init)
+    ores = oracle.track(ovol, depth, abi(intr), templ, init,
+                        oracle.TrackParams(n_iters=6, k_sched=ks, decim_sched=ds, update_mode=1, compose_mode=1))
+    assert status == pf.PF_OK and not ores.lost
+    os_ = ores.stats
+    assert list(st["n_eval"]) == list(os_["n_eval"])
+    strict = 0
+    for i in range(6):
+        if not os_["best_gap"][i] > 3e-5:
+            break
+        strict += 1
+        assert st["best"][i] == os_["best"][i], i
+        assert st["n_valid0"][i] == os_["n_valid0"][i], i
+        assert abs(st["E0"][i] - os_["E0"][i]) <= 1e-5 * os_["E0"][i], i
+    assert strict >= 2
+    assert pose_trans_err(pose, ores.pose) <= 1e-4 and pose_rot_err(pose, ores.pose) <= 1e-4
 
 
 def test_track_decimated_schedule(pf):
