@@ -362,18 +362,43 @@ struct FitArgs {
     int iter;
 };
 
+// Rodrigues' formula R = I + a [w]x + b [w]x^2 with a = sin(th)/th and
+// b = (1 - cos th)/th^2, th = |w|.  SERIES (the chunk build's form): up to
+// th = 1 rad both come from their Taylor series in th^2 (a = sum (-th^2)^n /
+// (2n+1)!, b = sum (-th^2)^n / (2n+2)!, nine terms each: the first omitted
+// term is below 1e-17, and both agree with the closed form to ~1e-16
+// relative), which needs no square root, division or trigonometric call:
+// the search's rotations are a few degrees, and the FP64 chain of each
+// particle's construction is that kernel's latency.  Otherwise the closed
+// form (its first terms below th = 1e-8).
+template <bool SERIES = false>
 __device__ inline void so3_exp_d(const double w[3], double R[9])
 {
     const double th2 = w[0] * w[0] + w[1] * w[1] + w[2] * w[2];
-    const double th = sqrt(th2);
     double a, b;
-    if (th < 1e-8) {
-        a = 1.0 - th2 / 6.0;
-        b = 0.5 - th2 / 24.0;
+    if (SERIES && th2 <= 1.0) {
+        const double ca[9] = {1.0, -0.16666666666666666, 0.008333333333333333, -0.0001984126984126984,
+                              2.7557319223985893e-06, -2.505210838544172e-08, 1.6059043836821613e-10,
+                              -7.647163731819816e-13, 2.8114572543455206e-15};  // (-1)^n / (2n+1)!
+        const double cb[9] = {0.5, -0.041666666666666664, 0.001388888888888889, -2.48015873015873e-05,
+                              2.755731922398589e-07, -2.08767569878681e-09, 1.1470745597729725e-11,
+                              -4.779477332387385e-14, 1.5619206968586225e-16};  // (-1)^n / (2n+2)!
+        a = ca[8];
+        b = cb[8];
+        for (int n = 7; n >= 0; --n) {
+            a = fma(a, th2, ca[n]);
+            b = fma(b, th2, cb[n]);
+        }
     } else {
-        double sh = sin(0.5 * th), ch = cos(0.5 * th);
-        a = 2.0 * sh * ch / th;
-        b = 2.0 * sh * sh / th2;
+        const double th = sqrt(th2);
+        if (th < 1e-8) {
+            a = 1.0 - th2 / 6.0;
+            b = 0.5 - th2 / 24.0;
+        } else {
+            double sh = sin(0.5 * th), ch = cos(0.5 * th);
+            a = 2.0 * sh * ch / th;
+            b = 2.0 * sh * sh / th2;
+        }
     }
     R[0] = 1.0 - b * (w[1] * w[1] + w[2] * w[2]);
     R[1] = -a * w[2] + b * w[0] * w[1];
@@ -432,7 +457,7 @@ constexpr int kMagicBits = 0x4b400000;  // bits of 1.5 * 2^23
 constexpr int kNeverValid = 0x7fffffff;  // magic of a particle that reaches no cell
 
 // Camera-to-world pose of particle k in FP64.
-template <int SRC>
+template <int SRC, bool SERIES = false>
 __device__ inline void particle_pose(const FitArgs& a, int k, double R[9], double tw[3])
 {
     if (SRC == SRC_POSES) {
@@ -453,7 +478,7 @@ __device__ inline void particle_pose(const FitArgs& a, int k, double R[9], doubl
             const double wr = a.st->s[0] * kPi / 180.0, wt = a.st->s[1] / 100.0;
             const double dw[3] = {wr * (double)u[0], wr * (double)u[1], wr * (double)u[2]};
             double dR[9];
-            so3_exp_d(dw, dR);
+            so3_exp_d<SERIES>(dw, dR);
             for (int r = 0; r < 3; ++r) {
                 for (int c = 0; c < 3; ++c)
                     R[3 * r + c] = dR[3 * r] * P[c] + dR[3 * r + 1] * P[4 + c] + dR[3 * r + 2] * P[8 + c];
@@ -475,14 +500,23 @@ struct PlainXf {
 // Particles k_begin .. k_begin+kc-1 into shared memory, and the chunk's
 // reference matrix A_ref (its first particle) as hi and lo floats; with
 // sAbs, also each particle's plain float transform.
-template <int SRC>
+// CHUNK (the chunk build kernel): the series form of the exponential, and
+// thread 0's pose (the chunk's first particle) passed to the other threads
+// by shuffles instead of each thread forming it again.
+template <int SRC, bool CHUNK = false>
 __device__ void build_particles(const FitArgs& a, int k_begin, int kc, Particle* sP, float* sRef, PlainXf* sAbs)
 {
-    const int t = threadIdx.x;
+    const int t = threadIdx.x;  // (kc <= KC = 32: one warp)
     if (t >= kc) return;
     double R[9], tw[3], R0[9], t0[3];
-    particle_pose<SRC>(a, k_begin + t, R, tw);
-    particle_pose<SRC>(a, k_begin, R0, t0);
+    particle_pose<SRC, CHUNK>(a, k_begin + t, R, tw);
+    if (CHUNK) {
+        const unsigned lanes = kc >= 32 ? 0xffffffffu : (1u << kc) - 1u;
+        for (int q = 0; q < 9; ++q) R0[q] = __shfl_sync(lanes, R[q], 0);
+        for (int r = 0; r < 3; ++r) t0[r] = __shfl_sync(lanes, tw[r], 0);
+    } else {
+        particle_pose<SRC>(a, k_begin, R0, t0);
+    }
     const double iv = 1.0 / a.vs;
     float d[9], b[3];
     int magic[3];
@@ -922,7 +956,7 @@ __global__ void __launch_bounds__(32) chunk_build_kernel(FitArgs a, ChunkData* o
     if (SRC != SRC_POSES && a.st->lost) return;  // the fitness launch skips every chunk then
     ChunkData& C = out[blockIdx.x];
     const int nx = a.nx, nxy = a.nx * a.ny;
-    build_particles<SRC>(a, k_begin, kc, C.P, C.ref, nullptr);
+    build_particles<SRC, true>(a, k_begin, kc, C.P, C.ref, nullptr);
     __syncwarp();
     const bool mine = t < kc;
     Particle P;
