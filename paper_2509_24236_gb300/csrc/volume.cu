@@ -48,7 +48,7 @@ struct IntegArgs {
     float plane[4][3];                  // inward normals of the four side planes of the frustum
     float zfar;                         // nodes deeper than this are never updated
     float radius;                       // bounding radius of a tile (+ margin)
-    int* tile_stamp;                    // tiles not culled get *stamp_dev (null: no cell view)
+    int* tile_stamp;                    // tiles with a changed node value get *stamp_dev (null: no cell view)
     const int* stamp_dev;               // fusion counter on the device
     int tiles[3];                       // fusion tiles per axis
     FusionList list;                    // tiles that survive the cull, with their bases
@@ -70,10 +70,10 @@ __global__ void fusion_begin_kernel(FusionList list, int* stamp_counter)
 // position of the tile's first node, X_c = R^T (X_w - t) with
 // X_w = origin + vs (i0, j0, k0), in FP64 -- kept as floats, the depth as a
 // hi + lo pair -- and the frustum cull of the tile's bounding sphere.  A tile
-// that survives is stamped and appended to the list (its position in the
-// list depends on scheduling; each tile's nodes are fused once whatever the
-// order, so the result does not).  Thread 0 also writes the per-index steps,
-// vs times the rows of R, which every tile shares.
+// that survives is appended to the list (its position in the list depends on
+// scheduling; each tile's nodes are fused once whatever the order, so the
+// result does not).  Thread 0 also writes the per-index steps, vs times the
+// rows of R, which every tile shares.
 __global__ void __launch_bounds__(256) fusion_tiles_kernel(IntegArgs a)
 {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -103,21 +103,35 @@ __global__ void __launch_bounds__(256) fusion_tiles_kernel(IntegArgs a)
         if (dd < -a.radius) skip = true;
     }
     if (skip) return;
-    if (a.tile_stamp) a.tile_stamp[t] = *a.stamp_dev;
     const float hi = (float)b[2];
     const int slot = atomicAdd(a.list.count, 1);
     a.list.tile[slot] = t;
     a.list.base[slot] = make_float4((float)b[0], (float)b[1], hi, (float)(b[2] - (double)hi));
 }
 
+template <typename T>
+__device__ __forceinline__ bool same_bits(T x, T y)
+{
+    unsigned bx = 0u, by = 0u;
+    memcpy(&bx, &x, sizeof(T));
+    memcpy(&by, &y, sizeof(T));
+    return bx == by;
+}
+
 // Fusion of the listed tiles; a fixed grid of CTAs walks the list.  Thread
 // (tx, ty) of a tile owns the column of TZ nodes (i0 + tx, j0 + ty, k0 + dz).
+// With a cell view, a tile where some node's stored value changed is stamped
+// with the fusion counter (by every thread that changed one: the same value);
+// a fused node whose value stays -- free space seen again, still outside the
+// band -- changes only its weight, which no cell record holds, so its tile's
+// records need no rewrite.
 template <typename TS, typename TW>
 __global__ void __launch_bounds__(TX * TY, 4) integrate_kernel(IntegArgs a)
 {
     TS* const tsdf = static_cast<TS*>(a.tsdf);
     TW* const weight = static_cast<TW*>(a.weight);
     const int n_active = *a.list.count;
+    const int stamp = a.tile_stamp ? *a.stamp_dev : 0;
     const int tx = threadIdx.x, ty = threadIdx.y;
     const float ai[3] = {a.list.step[0], a.list.step[1], a.list.step[2]};
     const float aj[3] = {a.list.step[3], a.list.step[4], a.list.step[5]};
@@ -134,6 +148,7 @@ __global__ void __launch_bounds__(TX * TY, 4) integrate_kernel(IntegArgs a)
         if (i >= a.nx || j >= a.ny) continue;
         const float bx_ = base.x, by_ = base.y, bz_hi = base.z, bz_lo = base.w;
         size_t idx = (size_t)i + (size_t)a.nx * j + plane_stride * k0;
+        bool changed = false;
         for (int dz = 0; dz < TZ; ++dz, idx += plane_stride) {
             const int k = k0 + dz;
             if (k >= a.nz) break;
@@ -154,12 +169,16 @@ __global__ void __launch_bounds__(TX * TY, 4) integrate_kernel(IntegArgs a)
             if (sdf < -a.trunc) continue;
             const float tt = fminf(1.0f, __fdiv_rn(sdf, a.trunc));
             const float w = pf_to_float(weight[idx]);
+            const TS old = tsdf[idx];
             float tn = tt;
-            if (w > 0.0f) tn = __fdiv_rn(fmaf(w, pf_decode(pf_to_float(tsdf[idx])), tt), w + 1.0f);
+            if (w > 0.0f) tn = __fdiv_rn(fmaf(w, pf_decode(pf_to_float(old)), tt), w + 1.0f);
             const float wn = fminf(w + 1.0f, a.max_weight);
-            tsdf[idx] = pf_from_float<TS>(pf_encode(tn, wn));
+            const TS stored = pf_from_float<TS>(pf_encode(tn, wn));
+            changed = changed || !same_bits(stored, old);
+            tsdf[idx] = stored;
             weight[idx] = pf_from_float<TW>(wn);
         }
+        if (changed && a.tile_stamp) a.tile_stamp[t] = stamp;
     }
 }
 
@@ -183,8 +202,8 @@ __global__ void fill_kernel(void* tsdf_, void* weight_, size_t n)
 // operation the fitness would do, so results are bit-identical, and a
 // non-finite corner still makes the interpolated value non-finite.  A cell
 // depends on the nodes of its own fusion tile and of the next tiles along
-// +x, +y, +z, so a tile is rewritten when any of those was reached by the
-// last fusion (or always, after a reset or upload).
+// +x, +y, +z, so a tile is rewritten when a node value of any of those was
+// changed by the last fusion (or always, after a reset or upload).
 struct RefreshArgs {
     const void* tsdf;
     void* cells;
@@ -198,8 +217,8 @@ struct RefreshArgs {
 };
 
 // One thread per tile: a tile's cells are rewritten when the tile or one of
-// its neighbours along +x, +y, +z (whose nodes its cells reach) was fused by
-// the last fusion, or always (all).  Order of the list as in
+// its neighbours along +x, +y, +z (whose nodes its cells reach) had a node
+// value changed by the last fusion, or always (all).  Order of the list as in
 // fusion_tiles_kernel: any, with the same result.
 __global__ void __launch_bounds__(256) refresh_tiles_kernel(RefreshArgs a)
 {
