@@ -41,7 +41,8 @@ def sources() -> list:
 
 
 def _inputs_mtime() -> float:
-    files = sources() + glob.glob(os.path.join(CSRC, "*.cuh")) + glob.glob(os.path.join(INCLUDE, "*.h"))
+    files = (sources() + glob.glob(os.path.join(CSRC, "*.cuh")) + glob.glob(os.path.join(CSRC, "*.h"))
+             + glob.glob(os.path.join(INCLUDE, "*.h")))
     files.append(os.path.abspath(__file__))
     return max(os.path.getmtime(f) for f in files)
 

@@ -45,6 +45,7 @@
 #include <vector>
 
 #include "pf_internal.cuh"
+#include "ptiles.h"
 
 namespace {
 
@@ -1673,51 +1674,16 @@ int device_sms(int dev)
     return n;
 }
 
-// Point tiles for a launch with `chunks` particle chunks over at most
-// `ne_max` evaluated points.  The CTA count is chosen to fill whole waves of
-// resident CTAs (PF_FIT_MIN_BLOCKS per SM): among 3.5 to 8.5 waves, the
-// count with the least time in waves x sub-tile passes per CTA (a partial
-// last wave, and a CTA's partial last sub-tile, cost whole ones), then the
-// fullest last wave, then the fewest waves -- on the 640x480 / 512^3 search,
-// 4 exact waves run 9% faster than 2.7 waves, and with the paper's 1/32
-// decimation (10240 particles x 9600 points) 5 tiles of two full passes beat
-// 7 tiles whose second pass is a third full.  Tiles never go below one
-// sub-tile of points; a launch too small for 3.5 waves takes as many tiles
-// as it has sub-tiles.
+// Point tiles of a launch (the rule and its bound: ptiles.h), for this
+// device's resident CTA slots.
 int choose_ptiles(int dev, int chunks, long long ne_max)
 {
-    const long long cap = (long long)device_sms(dev) * PF_FIT_MIN_BLOCKS;
-    const long long max_tiles = std::max(1LL, (ne_max + SUBTILE - 1) / SUBTILE);
-    long long best = 0, best_cost = 0;
-    double best_eff = 0.0, best_waves = 0.0;
-    for (long long t = 1; t <= max_tiles; ++t) {
-        const double waves = (double)(chunks * t) / (double)cap;
-        if (waves > 8.5) break;
-        if (waves < 3.5) continue;
-        const long long passes = (ne_max + t * SUBTILE - 1) / (t * SUBTILE);
-        const long long cost = (long long)std::ceil(waves) * passes;
-        const double eff = waves / std::ceil(waves);
-        if (best == 0 || cost < best_cost ||
-            (cost == best_cost && (eff > best_eff + 1e-9 || (eff > best_eff - 1e-9 && waves < best_waves)))) {
-            best = t;
-            best_cost = cost;
-            best_eff = eff;
-            best_waves = waves;
-        }
-    }
-    if (best == 0) best = std::min(max_tiles, std::max(1LL, (long long)std::ceil(3.5 * cap / chunks)));
-    return (int)best;
+    return pf::choose_ptiles_for((long long)device_sms(dev) * PF_FIT_MIN_BLOCKS, SUBTILE, chunks, ne_max);
 }
 
-// The most tiles choose_ptiles takes for `chunks` chunks over at most
-// `ne_max` points or any fewer (a decimated schedule): what the partial
-// sums are sized for.
 int ptiles_bound(int dev, int chunks, long long ne_max)
 {
-    const long long cap = (long long)device_sms(dev) * PF_FIT_MIN_BLOCKS;
-    const long long max_tiles = std::max(1LL, (ne_max + SUBTILE - 1) / SUBTILE);
-    const long long hi = std::max((long long)std::floor(8.5 * cap / chunks), (long long)std::ceil(3.5 * cap / chunks));
-    return (int)std::min(max_tiles, std::max(1LL, hi));
+    return pf::ptiles_bound_for((long long)device_sms(dev) * PF_FIT_MIN_BLOCKS, SUBTILE, chunks, ne_max);
 }
 
 // variant = layout + 4 * mapping (see pf_set_fitness_variant).  Measured on
